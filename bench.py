@@ -1,0 +1,441 @@
+#!/usr/bin/env python
+"""Benchmark of the CB-GMRES / FRSZ2 hot path on GB300.
+
+Default workload (one step = one pass of the basis hot path over the standalone basis
+configuration): a basis of 100 vectors x n = 2^24 values, N(0,1) * 2^k with k uniform in [-20, 20]
+per 32-value block (seed 1, unit-norm vectors), stored as FRSZ2 with l = 32. A step
+
+  1. compresses the step's vector w (n FP64 values) into the basis      (Fig. 1 steps 13-14)
+  2. h := V^T w over the 100 stored vectors, decoded in registers         (step 5)
+  3. w := w - V h over the 100 stored vectors, with ||w||^2              (steps 5-6)
+
+all through the C ABI on the current stream. `value` is the algorithmic HBM traffic of a step
+divided by its time (GB/s). The JSON line also carries the roofline of the dominant kernel, the
+oracle timed on host cores on a bounded sample (cpu_baseline), the same step through host
+buffers (e2e), the other storage formats, and the time to a 1e-10 relative residual of a full
+CB-GMRES solve with the FRSZ2 and the fp64 basis.
+
+`--impl reference` times the oracle (plain C, one host core) on a bounded sample of the same
+step. Under torchrun (N > 1) every rank runs its own replica of the workload (weak scaling, no
+collective on the data path); rank 0 prints the line.
+"""
+from __future__ import annotations
+
+import argparse
+import ctypes
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "time to 1e-10 rel. residual, FRSZ2 vs fp64 basis; basis GB/s; p99 latency"
+FMT_CODES = {"fp64": 0, "fp32": 1, "fp16": 2, "bf16": 3, "frsz2": 4}
+VALUE_BYTES = {"fp64": 8, "fp32": 4, "fp16": 2, "bf16": 2}
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "of measured (MEASURED_PEAKS.json hbm_gbs, torch copy)"
+    return 6800.0, "of fallback (6.8 TB/s)"
+
+
+def stored_bytes(fmt: str, l: int, n: int) -> int:
+    """Bytes of one stored vector that a basis kernel reads: Eq. 3 for FRSZ2, n x width for casts."""
+    if fmt == "frsz2":
+        nb = (n + 31) // 32
+        return nb * l * 4 + nb * 4
+    return n * VALUE_BYTES[fmt]
+
+
+def step_bytes(fmt: str, l: int, n: int, nvec: int):
+    vb = stored_bytes(fmt, l, n)
+    return {"store": 8 * n + vb, "dot": nvec * vb + 8 * n, "update": nvec * vb + 16 * n}
+
+
+def traffic_from_profiles(kernel_tag: str):
+    """Per-launch DRAM bytes of a kernel from the committed ncu summary (profiles/*.txt), if any."""
+    d = os.path.join(ROOT, "profiles")
+    if not os.path.isdir(d):
+        return None
+    for name in sorted(os.listdir(d)):
+        if not name.endswith(".txt"):
+            continue
+        with open(os.path.join(d, name)) as f:
+            for line in f:
+                if line.startswith("traffic_bytes_per_full_launch") and kernel_tag in line:
+                    try:
+                        return float(line.split("=")[1].split()[0])
+                    except (IndexError, ValueError):
+                        return None
+    return None
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle-reason samples every 200 ms while running."""
+
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.dev = device_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.dev), f"--query-gpu={self.QUERY}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"], "samples": 0}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons, power = [], [], set(), []
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    smax.append(float(parts[2]))
+                    power.append(float(parts[3]))
+                except ValueError:
+                    continue
+                for nm, v in zip(names, parts[5:9]):
+                    if v.lower() == "active":
+                        reasons.add(nm)
+        os.unlink(self.path)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"], "samples": 0}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm), "power_w_max": max(power)}
+
+
+# ------------------------------------------------------------------------------------------------
+# GPU arm
+# ------------------------------------------------------------------------------------------------
+
+def make_basis(pkg, torch, fmt, l, n, nvec, device):
+    B = pkg.BasisStorage(n, nvec + 1, FMT_CODES[fmt], l, device=device)
+    import workloads
+
+    for i in range(nvec):
+        B.store(i, workloads.basis_vector(i, n, seed=1, device=device))
+    w = workloads.basis_vector(nvec, n, seed=1, device=device)
+    torch.cuda.synchronize(device)
+    return B, w
+
+
+def time_steps(pkg, torch, B, w, nvec, steps, warmup, per_kernel=False):
+    """Times `steps` steps on the current stream with CUDA events; returns (total_ms, per-kernel ms)."""
+    stream = torch.cuda.current_stream()
+    h = torch.empty(nvec, dtype=torch.float64, device=w.device)
+    nrm = torch.empty(1, dtype=torch.float64, device=w.device)
+    work = B.work(nvec)
+
+    def one():
+        B.store(nvec, w)
+        B.dot(nvec, w, out=h, work=work)
+        B.update(nvec, h, w, norm2=nrm, work=work)
+
+    for _ in range(warmup):
+        one()
+    torch.cuda.synchronize()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    kev = []
+    if per_kernel:
+        kev = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(steps)]
+    ev[0].record(stream)
+    for s in range(steps):
+        if per_kernel:
+            e = kev[s]
+            e[0].record(stream)
+            B.store(nvec, w)
+            e[1].record(stream)
+            B.dot(nvec, w, out=h, work=work)
+            e[2].record(stream)
+            B.update(nvec, h, w, norm2=nrm, work=work)
+            e[3].record(stream)
+        else:
+            one()
+    ev[1].record(stream)
+    torch.cuda.synchronize()
+    total = ev[0].elapsed_time(ev[1])
+    kms = None
+    if per_kernel:
+        kms = {"store": float(np.mean([e[0].elapsed_time(e[1]) for e in kev])),
+               "dot": float(np.mean([e[1].elapsed_time(e[2]) for e in kev])),
+               "update": float(np.mean([e[2].elapsed_time(e[3]) for e in kev]))}
+    return total, kms
+
+
+def time_e2e(pkg, torch, B, w, nvec, steps, warmup):
+    """The same step through host buffers: w arrives from pinned host memory and h, ||w||^2 go back."""
+    stream = torch.cuda.current_stream()
+    n = w.numel()
+    w_host = w.cpu().pin_memory()
+    h_host = torch.empty(nvec, dtype=torch.float64).pin_memory()
+    nrm_host = torch.empty(1, dtype=torch.float64).pin_memory()
+    wd = torch.empty_like(w)
+    h = torch.empty(nvec, dtype=torch.float64, device=w.device)
+    nrm = torch.empty(1, dtype=torch.float64, device=w.device)
+    work = B.work(nvec)
+
+    def one():
+        wd.copy_(w_host, non_blocking=True)
+        B.store(nvec, wd)
+        B.dot(nvec, wd, out=h, work=work)
+        B.update(nvec, h, wd, norm2=nrm, work=work)
+        h_host.copy_(h, non_blocking=True)
+        nrm_host.copy_(nrm, non_blocking=True)
+
+    for _ in range(warmup):
+        one()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        one()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1), 8 * n, 8 * nvec + 8
+
+
+def time_to_tol(pkg, torch, device, repeats=3):
+    """Full CB-GMRES solves to a 1e-10 relative residual on the 64x64 convection-diffusion system
+    (restart 50), FRSZ2-32 vs fp64 basis, through cbgmres_solve with device-resident b and x."""
+    import workloads
+
+    A = workloads.convdiff(64, 2, (1.0, 0.5), 10.0, device=device)
+    xt = workloads.uniform_vector(A.n, 0, device=device)
+    b = pkg.spmv(A.row_ptr, A.col, A.vals, xt).clone()
+    out = {}
+    for fmt in ("fp64", "frsz2"):
+        S = pkg.Solver(A.row_ptr, A.col, A.vals, restart=50, tol=1e-10, fmt=fmt, frsz2_bits=32)
+        ts, r = [], None
+        for _ in range(repeats + 1):
+            x = torch.zeros(A.n, dtype=torch.float64, device=device)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            r = S.solve(b, x)
+            ts.append(time.perf_counter() - t0)
+        S.close()
+        out[fmt] = {"seconds": float(np.median(ts[1:])), "iters": r.iters, "converged": r.converged,
+                    "true_rrn": r.true_rrn}
+    out["speedup_frsz2_vs_fp64"] = out["fp64"]["seconds"] / out["frsz2"]["seconds"]
+    out["config"] = "2D 5-point convection-diffusion 64x64 (n=4096), wind (1,0.5)*10, b = A x_true, restart 50"
+    return out
+
+
+# ------------------------------------------------------------------------------------------------
+# Oracle (CPU) arm
+# ------------------------------------------------------------------------------------------------
+
+def oracle_step_setup(n: int, nvec: int):
+    import oracle
+    import workloads
+
+    oracle.build()
+    V = [oracle.encode(workloads.basis_vector(i, n, seed=1).numpy(), oracle.FRSZ2, 32) for i in range(nvec)]
+    w = workloads.basis_vector(nvec, n, seed=1).numpy().copy()
+    return oracle, V, w
+
+
+def oracle_step(oracle, V, w, n, nvec):
+    """The benchmark step on the host with the oracle as it stands: compress w, decode every stored
+    vector and take the sequential dot, then decode again and subtract (sequential axpy)."""
+    oracle.encode(w, oracle.FRSZ2, 32)
+    h = np.empty(nvec)
+    for i, (vals, exps) in enumerate(V):
+        h[i] = oracle.dot(oracle.decode(vals, exps, n, oracle.FRSZ2, 32), w)
+    for i, (vals, exps) in enumerate(V):
+        oracle.axpy(-h[i], oracle.decode(vals, exps, n, oracle.FRSZ2, 32), w)
+    return h, oracle.dot(w, w)
+
+
+def oracle_rate(n: int, nvec: int, steps: int, warmup: int):
+    oracle, V, w = oracle_step_setup(n, nvec)
+    for _ in range(warmup):
+        oracle_step(oracle, V, w, n, nvec)
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        oracle_step(oracle, V, w, n, nvec)
+    dt = time.perf_counter() - t0
+    byt = sum(step_bytes("frsz2", 32, n, nvec).values()) * steps
+    return byt / dt / 1e9, dt
+
+
+def choose_oracle_sample(nvec: int, steps_total: int, budget_s: float, n_full: int) -> int:
+    """Largest sample (a multiple of 128 values) whose steps_total steps fit in budget_s."""
+    n0 = 4096
+    _, dt = oracle_rate(n0, nvec, 1, 0)
+    per_value = dt / n0
+    n = int(budget_s / max(steps_total, 1) / per_value)
+    n = max(128, min(n_full, n // 128 * 128))
+    return n
+
+
+def cpu_baseline(n_full: int, nvec: int):
+    n = choose_oracle_sample(nvec, 3, 15.0, n_full)
+    gbs, dt = oracle_rate(n, nvec, 3, 0)
+    return {"value": gbs, "unit": "GB/s", "cores": 1, "kind": "oracle",
+            "sample": f"3 steps over {nvec} x {n} values ({n / n_full:.5f} of the workload's n), plain C oracle, "
+                      f"{dt:.1f} s", "nproc": os.cpu_count()}
+
+
+# ------------------------------------------------------------------------------------------------
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=300)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--n", type=int, default=1 << 24)
+    ap.add_argument("--nvec", type=int, default=100)
+    ap.add_argument("--fmt", default="frsz2")
+    ap.add_argument("--bits", type=int, default=32)
+    ap.add_argument("--no-extras", action="store_true", help="skip the format sweep, e2e, solve and CPU legs")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    workload = (f"basis kernels: {args.fmt}{'_' + str(args.bits) if args.fmt == 'frsz2' else ''} store + fused "
+                f"decode-dot + decode-update over {args.nvec} x {args.n} values (N(0,1)*2^k per 32-block, "
+                f"k in [-20,20], seed 1, unit-norm vectors)")
+
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        budget = 150.0
+        n = choose_oracle_sample(args.nvec, args.steps + args.warmup, budget, args.n)
+        gbs, dt = oracle_rate(n, args.nvec, args.steps, args.warmup)
+        line = {"impl": "reference", "metric": METRIC, "value": gbs, "unit": "GB/s", "n_gpus": args.gpus,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3 / args.steps,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+                "data": "synthetic",
+                "config": {"workload": workload, "n": args.n, "nvec": args.nvec, "oracle_sample_n": n},
+                "cpu_baseline": {"value": gbs, "unit": "GB/s", "cores": 1, "kind": "oracle",
+                                 "sample": f"each step over {args.nvec} x {n} values of the workload"},
+                "e2e": {"value": gbs, "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+        print(json.dumps(line))
+        return
+
+    import torch
+
+    import paper_2409_15468_gb300 as pkg
+
+    pkg.load()
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    device = torch.device("cuda", local if world > 1 else torch.cuda.current_device())
+    torch.cuda.set_device(device)
+    peak, peak_src = load_peaks()
+    fmt, l = args.fmt, args.bits
+    B, w = make_basis(pkg, torch, fmt, l, args.n, args.nvec, device)
+    sb = step_bytes(fmt, l, args.n, args.nvec)
+    per_step = sum(sb.values())
+
+    # main timed region (with clocks sampled during it)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    sampler = ClockSampler(device.index if device.index is not None else 0).start() if rank == 0 else None
+    time.sleep(0.3)
+    total_ms, _ = time_steps(pkg, torch, B, w, args.nvec, args.steps, args.warmup)
+    if dist:
+        t = torch.tensor([total_ms], device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    # per-kernel durations for the roofline (a separate pass, same launches)
+    _, kms = time_steps(pkg, torch, B, w, args.nvec, max(20, min(args.steps, 100)), 2, per_kernel=True)
+    clocks = sampler.stop() if sampler else None
+    if rank != 0:
+        dist.barrier()
+        dist.destroy_process_group()
+        return
+
+    value = world * per_step * args.steps / (total_ms * 1e-3) / 1e9
+    dom = max(("dot", "update"), key=lambda k: kms[k])
+    achieved = sb[dom] / (kms[dom] * 1e-3) / 1e9
+    tag = f"{dom}_{fmt}{l if fmt == 'frsz2' else ''}"
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "traffic": traffic_from_profiles(tag), "kernel": f"k_{dom}_{fmt}<{l}>" if fmt == "frsz2" else dom,
+                "peak_source": peak_src,
+                "per_kernel_ms": kms,
+                "per_kernel_gbs": {k: sb[k] / (kms[k] * 1e-3) / 1e9 for k in kms}}
+    line = {"metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": workload, "n": args.n, "nvec": args.nvec, "format": fmt, "frsz2_bits": l,
+                       "bytes_per_step": per_step, "l2": "inputs larger than L2 (no flush needed)",
+                       "parallelism": f"replicas x{world}" if world > 1 else "1 GPU"},
+            "roofline": roofline, "gpu_launches": 3 * args.steps, "clocks": clocks}
+
+    if not args.no_extras:
+        # e2e through host buffers
+        e_ms, h2d, d2h = time_e2e(pkg, torch, B, w, args.nvec, max(20, args.steps // 5), 3)
+        e_steps = max(20, args.steps // 5)
+        line["e2e"] = {"value": per_step * e_steps / (e_ms * 1e-3) / 1e9, "unit": "GB/s", "h2d_bytes_per_step": h2d,
+                       "d2h_bytes_per_step": d2h, "steps": e_steps}
+        del B, w
+        torch.cuda.empty_cache()
+        # the other storage formats on the same step
+        fmts = {}
+        for f2, l2 in (("fp64", 32), ("fp32", 32), ("fp16", 32), ("bf16", 32), ("frsz2", 16), ("frsz2", 21),
+                       ("frsz2", 32)):
+            B2, w2 = make_basis(pkg, torch, f2, l2, args.n, args.nvec, device)
+            steps2 = max(10, min(args.steps, 50))
+            ms2, k2 = time_steps(pkg, torch, B2, w2, args.nvec, steps2, 3, per_kernel=True)
+            sb2 = step_bytes(f2, l2, args.n, args.nvec)
+            name = f2 if f2 != "frsz2" else f"frsz2_{l2}"
+            fmts[name] = {"gbs": sum(sb2.values()) * steps2 / (ms2 * 1e-3) / 1e9,
+                          "ms_per_step": ms2 / steps2,
+                          "frac_of_peak": sum(sb2.values()) * steps2 / (ms2 * 1e-3) / 1e9 / peak,
+                          "dot_gbs": sb2["dot"] / (k2["dot"] * 1e-3) / 1e9,
+                          "update_gbs": sb2["update"] / (k2["update"] * 1e-3) / 1e9}
+            del B2, w2
+            torch.cuda.empty_cache()
+        fmts["speedup_frsz2_32_vs_fp64_per_step"] = fmts["fp64"]["ms_per_step"] / fmts["frsz2_32"]["ms_per_step"]
+        line["formats"] = fmts
+        line["time_to_tol"] = time_to_tol(pkg, torch, device)
+        line["cpu_baseline"] = cpu_baseline(args.n, args.nvec)
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+    print(json.dumps(line))
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,203 @@
+/* cbgmres.h - C ABI of the GB300 (sm_103a) Compressed-Basis GMRES library with the FRSZ2 block
+ * compressor of arXiv 2409.15468 ("FRSZ2 for In-Register Block Compression Inside GMRES on GPUs").
+ *
+ * Conventions for every entry point:
+ *   - Pointers named d_* are CUDA device pointers on the current device; h_* are host pointers.
+ *     The library never frees or retains caller memory beyond the call, except the CSR arrays
+ *     handed to cbgmres_create, which the context borrows until cbgmres_destroy.
+ *   - `stream` is a cudaStream_t (NULL = the legacy default stream). Work is enqueued on it; calls
+ *     return without synchronising unless stated otherwise.
+ *   - Every call returns CBG_OK (0) or a negative CBG_ERR_* status and never throws. The message
+ *     of the last failure on the calling thread is available from cbg_last_error().
+ *   - There is no CPU fallback: without a usable CUDA device every compute call fails with
+ *     CBG_ERR_CUDA.
+ *
+ * Storage formats of the Krylov basis (Compression Configuration: float64, float32 and float16
+ * storage with FP64 arithmetic; bfloat16 is one more cast; FRSZ2 per the Design section). All
+ * arithmetic is FP64 or exact integer arithmetic on the stored codes; the format only changes
+ * how the basis sits in memory.
+ */
+#ifndef CBGMRES_H
+#define CBGMRES_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes --------------------------------------------------------------------------- */
+#define CBG_OK 0
+#define CBG_ERR_INVALID_ARG (-1)  /* an argument failed validation; nothing was enqueued */
+#define CBG_ERR_CUDA (-2)         /* a CUDA runtime call failed (no device, launch failure, ...) */
+#define CBG_ERR_OOM (-3)          /* device allocation failed */
+#define CBG_ERR_NONFINITE (-4)    /* a norm or residual became NaN or infinite during a solve */
+#define CBG_ERR_NOT_CONVERGED (-5) /* max_iters reached; x and the result are still written */
+#define CBG_ERR_TIMEOUT (-6)      /* a bounded device-side wait expired; the context is unusable */
+#define CBG_ERR_BAD_MATRIX (-7)   /* CSR row pointers not monotone or a column index out of range */
+#define CBG_ERR_STATE (-8)        /* stepwise call out of order (advance before start, ...) */
+
+/* ---- basis storage formats ------------------------------------------------------------------ */
+typedef enum cbg_format {
+  CBG_FP64 = 0,  /* IEEE binary64 */
+  CBG_FP32 = 1,  /* IEEE binary32, round-to-nearest-even from FP64 */
+  CBG_FP16 = 2,  /* IEEE binary16, round-to-nearest-even from FP64 */
+  CBG_BF16 = 3,  /* bfloat16, round-to-nearest-even from FP64 */
+  CBG_FRSZ2 = 4  /* FRSZ2 with block size 32 and l-bit codes, l in {16, 21, 32} */
+} cbg_format;
+
+/* ---- FRSZ2 codec (Design section: Eq. 2, Eq. 3, Compression steps 1-6, Decompression 1-4) -----
+ * Layout of n values: ceil(n/32) exponent words (uint32, the raw biased IEEE exponent field of
+ * the block maximum) and, separately, ceil(n/32)*l code words (uint32). Code i of a block occupies
+ * bits [i*l, (i+1)*l) of the block's little-endian bit stream; bit l-1 is the sign, bit l-2 the
+ * integer bit, then l-2 fraction bits (Eq. 2); values are truncated toward zero to the block's
+ * quantum 2^(max(e_max,1) - 1023 - (l-2)). The last block is padded with +0.0. */
+
+/* Bytes of Eq. 3 for n values at code width l (code-size term read as ceil(32*l/32) words per
+ * block, consistent with the paper's 33 bits per value for l = 32). Returns -1 for a bad l or n. */
+int64_t cbg_frsz2_bytes(int64_t n, int32_t l);
+
+/* Compresses d_src[0..n) into d_exps[ceil(n/32)] and d_codes[ceil(n/32)*l] (Compression,
+ * steps 1-6: one warp per 32-value block, warp-wide maximum of the exponent fields).
+ * Inputs must be finite (Krylov values lie in [-1, 1]); the output for NaN or Inf is unspecified.
+ * d_src must be 8-byte aligned, d_exps and d_codes 4-byte aligned. */
+int cbg_frsz2_compress(const double* d_src, int64_t n, int32_t l, uint32_t* d_exps, uint32_t* d_codes,
+                       void* stream);
+
+/* Decompresses into d_dst[0..n) (Decompression, steps 1-4; random access by block). */
+int cbg_frsz2_decompress(const uint32_t* d_exps, const uint32_t* d_codes, int64_t n, int32_t l, double* d_dst,
+                         void* stream);
+
+/* ---- basis layout --------------------------------------------------------------------------- *
+ * A basis is nvec vectors of n values stored in one format. Vector i keeps its values (cast bits
+ * or FRSZ2 codes) at vals + i*vals_stride bytes and, for FRSZ2, its exponent words at
+ * exps + i*exps_stride bytes. The fused basis kernels stream the basis with 16-byte bulk copies,
+ * so: vals, exps and both strides must be multiples of 256 bytes, and each vector's arrays must
+ * hold ceil(n/128)*4 blocks of 32 values (the format's block rounded up to 4 blocks), the
+ * padding being readable memory (its contents are ignored). cbg_basis_layout gives the minimal
+ * strides. */
+typedef struct cbg_basis {
+  int32_t fmt;         /* cbg_format */
+  int32_t frsz2_bits;  /* l when fmt == CBG_FRSZ2, ignored otherwise */
+  int64_t n;           /* values per vector */
+  void* vals;          /* device pointer to vector 0's values / codes */
+  int64_t vals_stride; /* bytes between consecutive vectors' values */
+  uint32_t* exps;      /* device pointer to vector 0's exponent words (FRSZ2), else NULL */
+  int64_t exps_stride; /* bytes between consecutive vectors' exponent arrays */
+} cbg_basis;
+
+/* Minimal strides (bytes) of one basis vector; exps_stride is 0 for cast formats. */
+int cbg_basis_layout(int64_t n, int32_t fmt, int32_t l, int64_t* vals_stride, int64_t* exps_stride);
+
+/* Stores d_src[0..n) as vector `slot` of the basis: FRSZ2 compression or a round-to-nearest-even
+ * cast from FP64 (Fig. 1 steps 1 and 14, highlighted: appending a vector to the compressed basis). */
+int cbg_basis_store(const cbg_basis* basis, int32_t slot, const double* d_src, void* stream);
+
+/* Decodes basis vector `slot` into d_dst[0..n) (a read through the accessor: Implementation and
+ * synthetic performance subsection). */
+int cbg_basis_load(const cbg_basis* basis, int32_t slot, double* d_dst, void* stream);
+
+/* Scratch bytes that cbg_basis_dot / cbg_basis_update need for up to nvec vectors of n values. */
+size_t cbg_basis_work_bytes(int64_t n, int32_t nvec);
+
+/* d_h[i] = sum_k vhat_i[k] * d_w[k] for i in [0, nvec): the classical Gram-Schmidt projections
+ * h_{1:j} := V_j^T w of Fig. 1 step 5 (highlighted), reading the stored basis and decoding it in
+ * registers. FRSZ2 blocks are multiplied exactly in integer arithmetic against a 54-bit
+ * block-fixed-point copy of w and accumulated in FP64 across blocks; cast formats accumulate in
+ * FP64. Error bound: 2^-53 * sum_b max_{k in b}|w_k| * sum_{k in b}|vhat_k| plus FP64 summation
+ * error over at most about 2^6 sequential terms. d_work: cbg_basis_work_bytes(n, nvec) bytes,
+ * 256-byte aligned, no initial contents required, not used concurrently by another call. */
+int cbg_basis_dot(const cbg_basis* basis, int32_t nvec, const double* d_w, double* d_h, void* d_work,
+                  size_t work_bytes, void* stream);
+
+/* d_w[k] -= sum_i vhat_i[k] * d_h[i] over i in [0, nvec): the update w := w - V_j h of Fig. 1
+ * step 5 (highlighted). The sum over i is exact in integer arithmetic for FRSZ2 (h scaled per
+ * block to a 54-bit fixed point), FP64 otherwise. If d_norm2 is not NULL it receives ||w||^2 after
+ * the update (the norm of step 6). d_work as for cbg_basis_dot. */
+int cbg_basis_update(const cbg_basis* basis, int32_t nvec, const double* d_h, double* d_w, double* d_norm2,
+                     void* d_work, size_t work_bytes, void* stream);
+
+/* ---- sparse matrix ---------------------------------------------------------------------------- */
+/* Checks a CSR matrix on the device: row_ptr[0] == 0, row_ptr[n] == nnz, row pointers monotone,
+ * every column in [0, n). Returns CBG_ERR_BAD_MATRIX otherwise. Synchronises the stream.
+ * cbg_spmv assumes a valid matrix (it does not check), cbgmres_create runs this check itself. */
+int cbg_csr_validate(int32_t n, int64_t nnz, const int32_t* d_row_ptr, const int32_t* d_col, void* stream);
+
+/* d_y = A d_x for the CSR matrix (int32 row pointers and columns, FP64 values): Fig. 1 step 3,
+ * w := A M^{-1} v with M = I (no preconditioner: Solver Configuration). If d_norm2 is not NULL it
+ * receives ||y||^2 (step 4). d_work: cbg_spmv_work_bytes(n) bytes. */
+size_t cbg_spmv_work_bytes(int32_t n);
+int cbg_spmv(int32_t n, const int32_t* d_row_ptr, const int32_t* d_col, const double* d_vals, const double* d_x,
+             double* d_y, double* d_norm2, void* d_work, size_t work_bytes, void* stream);
+
+/* ---- solver ----------------------------------------------------------------------------------- */
+typedef struct cbg_opts {
+  int32_t restart;    /* m, the number of basis vectors before a restart (Methodology: m = 100) */
+  int32_t fmt;        /* cbg_format of the Krylov basis */
+  int32_t frsz2_bits; /* l for CBG_FRSZ2: 16, 21 or 32 */
+  int32_t history;    /* nonzero: record the implicit relative residual after every Arnoldi step */
+  double tol;         /* target relative residual ||b - A x|| / ||b|| (Eq. 4) */
+  int64_t max_iters;  /* cap on Arnoldi steps */
+  double eta;         /* re-orthogonalisation threshold of Fig. 1 step 7 (default 1/sqrt(2)) */
+} cbg_opts;
+
+typedef struct cbg_result {
+  int64_t iters;       /* Arnoldi steps (new basis vectors) */
+  int64_t restarts;    /* completed restart cycles */
+  int64_t reorths;     /* steps that took the second Gram-Schmidt pass (Fig. 1 steps 7-11) */
+  int32_t converged;   /* explicit ||b - A x|| <= tol ||b|| reached */
+  int32_t status;      /* CBG_OK or the CBG_ERR_* the solve ended with */
+  double true_rrn;     /* last explicit ||b - A x|| / ||b|| (Eq. 4) */
+  double implicit_rrn; /* last |g_{j+1}| / ||b|| of the Givens recurrence */
+  double seconds;      /* wall time of the solve as seen by the host */
+} cbg_result;
+
+typedef struct cbg_ctx cbg_ctx;
+
+/* Fills defaults: restart 100, FRSZ2 with l = 32, tol 1e-10, max_iters 20000, eta 1/sqrt(2). */
+int cbg_opts_default(cbg_opts* opts);
+
+/* Device bytes a context of size n with these options allocates (HBM admission control). */
+size_t cbgmres_workspace_bytes(int32_t n, const cbg_opts* opts);
+
+/* Creates a solver for the n x n CSR matrix A (Solver Configuration: A and b are immutable inputs).
+ * The CSR arrays are borrowed and must stay valid until cbgmres_destroy. Validates the matrix on
+ * the device (monotone row pointers, columns in [0, n)) and returns CBG_ERR_BAD_MATRIX otherwise.
+ * Allocates cbgmres_workspace_bytes(n, opts) of device memory. `stream` is the stream all of the
+ * context's work goes to. Synchronises the stream. */
+int cbgmres_create(cbg_ctx** out, int32_t n, int64_t nnz, const int32_t* d_row_ptr, const int32_t* d_col,
+                   const double* d_vals, const cbg_opts* opts, void* stream);
+
+/* Solves A x = b (Fig. 1: restarted GMRES with the basis stored in opts->fmt). d_x holds x0 on
+ * entry (the paper starts from x0 = 0) and the approximation on exit. Synchronises the stream.
+ * Returns CBG_OK when converged, CBG_ERR_NOT_CONVERGED when max_iters was reached (x and *result
+ * still valid), or another CBG_ERR_*. *result may be NULL. */
+int cbgmres_solve(cbg_ctx* ctx, const double* d_b, double* d_x, cbg_result* result);
+
+/* Stepwise form of cbgmres_solve for a serving loop that interleaves several solves:
+ *   cbgmres_start    computes the initial residual and the first basis vector (Fig. 1 step 1);
+ *   cbgmres_advance  runs up to max_steps further Arnoldi steps, restarts included, and reports
+ *                    in *done whether the solve has finished (converged, failed or out of steps);
+ *   cbgmres_finish   fills the result and returns the solve's status.
+ * b and x must stay valid from start to finish. advance synchronises at the end of each cycle. */
+int cbgmres_start(cbg_ctx* ctx, const double* d_b, double* d_x);
+int cbgmres_advance(cbg_ctx* ctx, int32_t max_steps, int32_t* done);
+int cbgmres_finish(cbg_ctx* ctx, cbg_result* result);
+
+/* Copies up to cap recorded implicit relative residuals (opts.history != 0) to h_out. */
+int cbgmres_history(cbg_ctx* ctx, double* h_out, int64_t cap, int64_t* count);
+
+/* Frees the context's device memory. Accepts NULL. */
+int cbgmres_destroy(cbg_ctx* ctx);
+
+/* Message of the last failed call on this thread ("" if none). */
+const char* cbg_last_error(void);
+
+/* Library version string. */
+const char* cbg_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

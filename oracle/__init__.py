@@ -80,6 +80,7 @@ def lib():
             "orc_dot": (ctypes.c_double, [P, P, i64]),
             "orc_dot2": (ctypes.c_double, [P, P, i64]),
             "orc_nrm2": (ctypes.c_double, [P, i64]),
+            "orc_axpy": (None, [ctypes.c_double, P, P, i64]),
             "orc_spmv_csr": (None, [i32, P, P, P, P, P]),
             "orc_gmres": (ctypes.c_int, [i32, P, P, P, P, P, ctypes.POINTER(_Opts), ctypes.POINTER(_Result), P, P]),
             "orc_arnoldi_cycle": (ctypes.c_int, [i32, P, P, P, P, P, ctypes.POINTER(_Opts), P, P, P,
@@ -206,6 +207,14 @@ def dot2(a, b) -> float:
 def nrm2(a) -> float:
     a = _f64(a)
     return float(lib().orc_nrm2(_p(a), a.size))
+
+
+def axpy(alpha: float, x, y: np.ndarray) -> np.ndarray:
+    """y += alpha x in place (sequential FP64)."""
+    x = _f64(x)
+    assert y.dtype == np.float64 and y.flags.c_contiguous and y.size == x.size
+    lib().orc_axpy(float(alpha), _p(x), _p(y), x.size)
+    return y
 
 
 def spmv(row_ptr, col, vals, x) -> np.ndarray:

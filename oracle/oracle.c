@@ -325,6 +325,10 @@ double orc_dot2(const double* a, const double* b, int64_t n) {
 
 double orc_nrm2(const double* a, int64_t n) { return sqrt(orc_dot(a, a, n)); }
 
+void orc_axpy(double alpha, const double* x, double* y, int64_t n) {
+  for (int64_t k = 0; k < n; ++k) y[k] += alpha * x[k];
+}
+
 void orc_spmv_csr(int32_t n, const int32_t* row_ptr, const int32_t* col, const double* vals,
                   const double* x, double* y) {
   for (int32_t i = 0; i < n; ++i) {

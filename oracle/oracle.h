@@ -49,6 +49,7 @@ int orc_decode(const void* vals, const uint32_t* exps, int64_t n, int32_t fmt, i
 double orc_dot(const double* a, const double* b, int64_t n);   /* sequential sum of a_k*b_k */
 double orc_dot2(const double* a, const double* b, int64_t n);  /* compensated (twice-working-precision) */
 double orc_nrm2(const double* a, int64_t n);
+void orc_axpy(double alpha, const double* x, double* y, int64_t n); /* y += alpha x, sequential */
 void orc_spmv_csr(int32_t n, const int32_t* row_ptr, const int32_t* col, const double* vals,
                   const double* x, double* y);
 

@@ -1,0 +1,102 @@
+// Internal kernel launchers of the library (host side) and the small device structs they share.
+#pragma once
+
+#include "common.cuh"
+
+namespace cbg {
+
+constexpr int kMaxGrid = 4096;  // upper bound on CTAs of the reducing kernels (sizes partial buffers)
+
+// Skip a kernel (uniformly, at entry) when *stop != 0 or when *need == 0. Null pointers never skip.
+struct Gate {
+  const int* stop;
+  const int* need;
+};
+
+// What the last CTA of a norm-producing kernel does with the reduced ||.||^2.
+enum EpiMode { kEpiNone = 0, kEpiOmega = 1, kEpiPass1 = 2, kEpiPass2 = 3, kEpiResidual = 4 };
+
+struct NormEpilogue {
+  double* out;     // receives ||.||^2 when not null
+  SolverCtl* ctl;  // solver control block to update, or null
+  int mode;        // EpiMode
+};
+
+__device__ __forceinline__ void norm_epilogue(const NormEpilogue& e, double norm2, int* err) {
+  if (e.out) *e.out = norm2;
+  if (!e.ctl) return;
+  SolverCtl* c = e.ctl;
+  if (!isfinite(norm2)) {
+    atomicOr(err, kDevErrNonFinite);
+    c->stop = 1;
+  }
+  const double nrm = sqrt(norm2);
+  switch (e.mode) {
+    case kEpiOmega:  // Fig. 1 step 4
+      c->omega2 = norm2;
+      break;
+    case kEpiPass1: {  // step 6 and the test of step 7
+      c->hn2_first = norm2;
+      c->hn2 = norm2;
+      c->reorth = nrm < c->eta * sqrt(c->omega2) ? 1 : 0;
+      break;
+    }
+    case kEpiPass2:  // step 10
+      c->hn2 = norm2;
+      break;
+    case kEpiResidual:  // step 1: beta = ||r0||, v = r0 / beta
+      c->beta = nrm;
+      c->rcp = nrm > 0.0 ? 1.0 / nrm : 0.0;
+      break;
+    default:
+      break;
+  }
+}
+
+// ---- basis.cu -----------------------------------------------------------------------------------
+// out[i] = <vhat_i, w> for i < nvec. partials: kMaxGrid * nvec doubles. *counter must be 0.
+int launch_basis_dot(const BasisView& B, int nvec, const double* w, double* out, double* partials,
+                     unsigned int* counter, int* err, const Gate& gate, cudaStream_t stream);
+// w -= sum_i vhat_i h_i (h negated when `negate`), nvec from *nvec_dev when not null (then
+// nvec is the upper bound used to size shared memory). ||w||^2 goes to the epilogue.
+int launch_basis_update(const BasisView& B, int nvec, const int* nvec_dev, const double* h, int negate, double* w,
+                        double* partials, unsigned int* counter, int* err, const NormEpilogue& epi,
+                        const Gate& gate, cudaStream_t stream);
+
+// ---- codec.cu -----------------------------------------------------------------------------------
+// Stores src (times *rcp when rcp is not null, also written to vout) into basis vector `slot`.
+int launch_store(const BasisMut& B, int slot, const double* src, const double* rcp, double* vout, const Gate& gate,
+                 cudaStream_t stream);
+int launch_frsz2_compress(const double* src, int64_t n, int l, uint32_t* exps, uint32_t* codes, cudaStream_t stream);
+int launch_frsz2_decompress(const uint32_t* exps, const uint32_t* codes, int64_t n, int l, double* dst,
+                            cudaStream_t stream);
+int launch_load(const BasisView& B, int slot, double* dst, cudaStream_t stream);
+
+// ---- spmv.cu ------------------------------------------------------------------------------------
+// y = A x (or y = bsub - A x when bsub is not null); ||y||^2 to the epilogue. partials: kMaxGrid.
+int launch_spmv(int n, const int32_t* row_ptr, const int32_t* col, const double* vals, const double* x, double* y,
+                const double* bsub, double* partials, unsigned int* counter, int* err, const NormEpilogue& epi,
+                const Gate& gate, cudaStream_t stream);
+int launch_validate_csr(int n, int64_t nnz, const int32_t* row_ptr, const int32_t* col, int* err,
+                        cudaStream_t stream);
+int launch_sumsq(const double* x, int64_t n, double* partials, unsigned int* counter, int* err, double* out,
+                 cudaStream_t stream);
+
+// ---- solver.cu ----------------------------------------------------------------------------------
+struct GivensArgs {
+  SolverCtl* ctl;
+  double* H;     // (m+1) x m column-major, ld m+1: the Hessenberg matrix (before rotations)
+  double* R;     // the rotated copy
+  double* cs;
+  double* sn;
+  double* g;     // rotated right-hand side beta e1
+  const double* u;  // second-pass coefficients
+  double* hist;  // implicit RRN history (may be null)
+  int64_t hist_off;
+  int64_t hist_cap;
+  int m;
+};
+int launch_givens(const GivensArgs& a, int j, cudaStream_t stream);
+int launch_cycle_init(SolverCtl* ctl, double* g, int m, int steps_allowed, cudaStream_t stream);
+
+}  // namespace cbg

@@ -1,0 +1,140 @@
+// CSR sparse matrix-vector product w := A v (Fig. 1 step 3, M = I) with the norm of step 4 fused
+// into the epilogue, the residual r := b - A x of step 1, and the CSR validation done once when a
+// solver is created. The SpMV reads the uncompressed FP64 vector v: the paper highlights only the
+// basis accesses as compressed.
+//
+// One thread per row: the stencil matrices have ~7 nonzeros per row, so the rows of a warp cover a
+// contiguous stretch of the value and column arrays that L1 serves to the per-nonzero loads, and
+// the FP64 work is exactly one FMA per nonzero (GB300's FP64 rate is the other bound of this
+// kernel). Rows are strided over a grid sized to the SM count so that the norm partials stay few.
+#include "common.cuh"
+#include "kernels.cuh"
+
+namespace cbg {
+
+namespace {
+__device__ __forceinline__ bool gate_skip_s(const Gate& g) {
+  if (g.stop && *(volatile const int*)g.stop) return true;
+  if (g.need && !*(volatile const int*)g.need) return true;
+  return false;
+}
+}  // namespace
+
+__global__ void __launch_bounds__(256) k_spmv(int n, const int32_t* __restrict__ row_ptr,
+                                              const int32_t* __restrict__ col, const double* __restrict__ vals,
+                                              const double* __restrict__ x, double* __restrict__ y,
+                                              const double* __restrict__ bsub, double* __restrict__ partials,
+                                              unsigned int* counter, int* err, NormEpilogue epi, Gate gate) {
+  if (gate_skip_s(gate)) return;
+  __shared__ double red[8];
+  __shared__ int flag;
+  const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+  double nrm = 0.0;
+  const int stride = gridDim.x * blockDim.x;
+  for (int i = blockIdx.x * blockDim.x + t; i < n; i += stride) {
+    const int p0 = __ldg(row_ptr + i), p1 = __ldg(row_ptr + i + 1);
+    double s = 0.0;
+    for (int p = p0; p < p1; ++p) s = fma(__ldg(vals + p), __ldg(x + __ldg(col + p)), s);
+    if (bsub) s = bsub[i] - s;
+    y[i] = s;
+    nrm = fma(s, s, nrm);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) nrm += __shfl_xor_sync(0xffffffffu, nrm, o);
+  if (lane == 0) red[warp] = nrm;
+  __syncthreads();
+  if (t == 0) {
+    double s = 0.0;
+    for (int i = 0; i < 8; ++i) s += red[i];
+    partials[blockIdx.x] = s;
+  }
+  if (arrive_last(counter, gridDim.x, &flag)) {
+    if (warp == 0) {
+      const double s = warp_sum_strided(partials, gridDim.x, 1);
+      if (lane == 0) norm_epilogue(epi, s, err);
+    }
+    if (t == 0) *counter = 0;
+  }
+}
+
+__global__ void k_validate_csr(int n, int64_t nnz, const int32_t* __restrict__ row_ptr,
+                               const int32_t* __restrict__ col, int* err) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (tid == 0 && (row_ptr[0] != 0 || (int64_t)row_ptr[n] != nnz)) atomicOr(err, kDevErrBadMatrix);
+  for (int64_t i = tid; i < n; i += stride)
+    if (row_ptr[i] > row_ptr[i + 1]) atomicOr(err, kDevErrBadMatrix);
+  for (int64_t p = tid; p < nnz; p += stride) {
+    const int32_t c = col[p];
+    if (c < 0 || c >= n) atomicOr(err, kDevErrBadMatrix);
+  }
+}
+
+__global__ void __launch_bounds__(256) k_sumsq(const double* __restrict__ x, int64_t n, double* __restrict__ partials,
+                                               unsigned int* counter, int* err, double* out) {
+  __shared__ double red[8];
+  __shared__ int flag;
+  const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+  double nrm = 0.0;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + t; i < n; i += stride) nrm = fma(x[i], x[i], nrm);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) nrm += __shfl_xor_sync(0xffffffffu, nrm, o);
+  if (lane == 0) red[warp] = nrm;
+  __syncthreads();
+  if (t == 0) {
+    double s = 0.0;
+    for (int i = 0; i < 8; ++i) s += red[i];
+    partials[blockIdx.x] = s;
+  }
+  if (arrive_last(counter, gridDim.x, &flag)) {
+    if (warp == 0) {
+      const double s = warp_sum_strided(partials, gridDim.x, 1);
+      if (lane == 0) {
+        *out = s;
+        if (!isfinite(s)) atomicOr(err, kDevErrNonFinite);
+      }
+    }
+    if (t == 0) *counter = 0;
+  }
+}
+
+namespace {
+int grid_rows(int64_t n, int per_sm) {
+  DeviceInfo di;
+  if (device_info(&di)) return 1;
+  int64_t g = (n + 255) / 256;
+  const int64_t cap = (int64_t)di.sms * per_sm;
+  if (g > cap) g = cap;
+  if (g > kMaxGrid) g = kMaxGrid;
+  return g < 1 ? 1 : static_cast<int>(g);
+}
+}  // namespace
+
+int launch_spmv(int n, const int32_t* row_ptr, const int32_t* col, const double* vals, const double* x, double* y,
+                const double* bsub, double* partials, unsigned int* counter, int* err, const NormEpilogue& epi,
+                const Gate& gate, cudaStream_t stream) {
+  if (n <= 0) return CBG_OK;
+  const int grid = grid_rows(n, 8);
+  k_spmv<<<grid, 256, 0, stream>>>(n, row_ptr, col, vals, x, y, bsub, partials, counter, err, epi, gate);
+  cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? CBG_OK : cuda_fail(e, "spmv launch");
+}
+
+int launch_validate_csr(int n, int64_t nnz, const int32_t* row_ptr, const int32_t* col, int* err,
+                        cudaStream_t stream) {
+  const int grid = grid_rows(n > nnz ? n : nnz, 8);
+  k_validate_csr<<<grid, 256, 0, stream>>>(n, nnz, row_ptr, col, err);
+  cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? CBG_OK : cuda_fail(e, "csr validation launch");
+}
+
+int launch_sumsq(const double* x, int64_t n, double* partials, unsigned int* counter, int* err, double* out,
+                 cudaStream_t stream) {
+  const int grid = grid_rows(n, 4);
+  k_sumsq<<<grid, 256, 0, stream>>>(x, n, partials, counter, err, out);
+  cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? CBG_OK : cuda_fail(e, "sumsq launch");
+}
+
+}  // namespace cbg

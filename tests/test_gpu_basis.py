@@ -1,0 +1,106 @@
+"""GPU parity of the fused basis kernels against the oracle:
+
+* dot    h_i = sum_k vhat_i[k] w_k          (Fig. 1 step 5, V_j^T w)
+* update w_k - sum_i vhat_i[k] h_i          (Fig. 1 step 5, w - V_j h)
+
+The reference is the oracle's compensated (twice-working-precision) dot of the oracle-decoded basis,
+so the comparison measures the GPU's own error. The tolerance follows from the GPU arithmetic:
+FRSZ2 blocks are summed exactly against a round-to-nearest 54-bit block fixed point of w (error at
+most 2^-54 max_{k in b}|w_k| per unit of |vhat|), cross-block and cross-CTA sums are FP64 over a
+tree of depth < 64 (error < 2^-46 sum |vhat w|); the update's per-block fixed point of h_i 2^{q_ib}
+keeps 54 bits of the largest term. The tolerances below are those bounds with a factor-4 margin.
+"""
+import numpy as np
+import pytest
+import torch
+
+import workloads
+
+pytestmark = pytest.mark.gpu
+
+FORMATS = [(0, 32), (1, 32), (2, 32), (3, 32), (4, 16), (4, 21), (4, 32)]
+
+
+def make_basis(cbg, orc, n, nvec, fmt, l, seed):
+    # Krylov vectors have unit norm, so every value lies in [-1, 1] (Problem Formulation); the
+    # in-block exponent spread of N(0,1) 2^k, k in [-20, 20] per block, is kept.
+    V = workloads.basis_values(nvec, n, seed=seed).numpy()
+    V /= np.linalg.norm(V, axis=1, keepdims=True)
+    B = cbg.BasisStorage(n, nvec, fmt, l)
+    Vd = torch.from_numpy(V).cuda()
+    for i in range(nvec):
+        B.store(i, Vd[i].contiguous())
+    enc = [orc.encode(V[i], fmt, l) for i in range(nvec)]
+    Vhat = np.stack([orc.decode(v, e, n, fmt, l) for v, e in enc])
+    exps = np.stack([e for _, e in enc]) if fmt == 4 else None
+    return B, Vhat, exps
+
+
+def dot_tolerance(Vhat, w):
+    n = w.size
+    nb = (n + 31) // 32
+    wpad = np.zeros(nb * 32)
+    wpad[:n] = np.abs(w)
+    wmax = wpad.reshape(nb, 32).max(axis=1)
+    vpad = np.zeros((Vhat.shape[0], nb * 32))
+    vpad[:, :n] = np.abs(Vhat)
+    vabs_b = vpad.reshape(Vhat.shape[0], nb, 32).sum(axis=2)
+    s_abs = np.abs(Vhat) @ np.abs(w)
+    return 4 * (2.0 ** -46 * s_abs + 2.0 ** -54 * (vabs_b @ wmax)) + 1e-300
+
+
+@pytest.mark.parametrize("fmt,l", FORMATS)
+@pytest.mark.parametrize("n,nvec", [(1, 1), (77, 3), (4096, 1), (4096 + 45, 7), (70000, 20), (300000 + 13, 66),
+                                    (128 * 128 * 3 + 32 * 5, 9)])
+def test_dot(cbg, orc, fmt, l, n, nvec):
+    B, Vhat, _ = make_basis(cbg, orc, n, nvec, fmt, l, seed=n + nvec)
+    w = np.random.default_rng(n).standard_normal(n) * np.exp2(np.random.default_rng(n + 1).integers(-6, 6, n))
+    h = B.dot(nvec, torch.from_numpy(w).cuda()).cpu().numpy()
+    ref = orc.basis_dot(Vhat, w)
+    tol = dot_tolerance(Vhat, w)
+    assert np.all(np.abs(h - ref) <= tol), (np.abs(h - ref) / tol).max()
+
+
+@pytest.mark.parametrize("fmt,l", FORMATS)
+@pytest.mark.parametrize("n,nvec", [(1, 1), (77, 3), (4096 + 45, 7), (70000, 20), (30000 + 13, 66),
+                                    (20000, 100)])
+def test_update(cbg, orc, fmt, l, n, nvec):
+    B, Vhat, exps = make_basis(cbg, orc, n, nvec, fmt, l, seed=3 * n + nvec)
+    rng = np.random.default_rng(n + 5)
+    w = rng.standard_normal(n)
+    h = rng.standard_normal(nvec) * np.exp2(rng.integers(-30, 3, nvec))
+    wd = torch.from_numpy(w).cuda()
+    nrm = torch.zeros(1, dtype=torch.float64, device="cuda")
+    B.update(nvec, torch.from_numpy(h).cuda(), wd, norm2=nrm)
+    out = wd.cpu().numpy()
+    # reference on a sample of elements (all of them for small n)
+    idx = np.arange(n) if n <= 5000 else np.unique(np.concatenate([np.arange(64), n - 1 - np.arange(64),
+                                                                   rng.integers(0, n, 3000)]))
+    ref = orc.basis_update(Vhat[:, idx], h, w[idx])
+    terms = np.abs(Vhat[:, idx] * h[:, None])
+    # largest possible term of each value's block: |h_i| * 2^(block exponent + 1) for FRSZ2
+    if fmt == 4:
+        e = np.maximum(exps[:, idx // 32].astype(np.float64), 1.0)
+        tmax = (np.abs(h)[:, None] * np.exp2(e - 1023.0 + 1.0)).max(axis=0)
+    else:
+        tmax = terms.max(axis=0)
+    tol = 4 * (2.0 ** -50 * (np.abs(w[idx]) + terms.sum(axis=0)) + nvec * 2.0 ** -53 * tmax) + 1e-300
+    err = np.abs(out[idx] - ref)
+    assert np.all(err <= tol), (err / tol).max()
+    # the fused norm is ||w||^2 of the updated vector
+    assert abs(nrm.item() - orc.dot2(out, out)) <= 1e-12 * orc.dot2(out, out)
+
+
+def test_dot_after_update_orthogonal(cbg, orc):
+    """One classical Gram-Schmidt pass against an orthonormal FP64 basis leaves w orthogonal to it."""
+    n, nvec = 50000, 12
+    Q, _ = np.linalg.qr(np.random.default_rng(1).standard_normal((n, nvec)))
+    B = cbg.BasisStorage(n, nvec, 0)
+    Qd = torch.from_numpy(np.ascontiguousarray(Q.T)).cuda()
+    for i in range(nvec):
+        B.store(i, Qd[i].contiguous())
+    w = torch.from_numpy(np.random.default_rng(2).standard_normal(n)).cuda()
+    h = B.dot(nvec, w).clone()
+    B.update(nvec, h, w)
+    h2 = B.dot(nvec, w).cpu().numpy()
+    assert np.abs(h2).max() <= 1e-13 * np.linalg.norm(h.cpu().numpy())

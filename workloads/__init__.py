@@ -157,6 +157,21 @@ def basis_values(nvec: int, n: int, seed: int = 1, device="cpu", kmin: int = -20
     return x * scale
 
 
+def basis_vector(i: int, n: int, seed: int = 1, device="cpu", kmin: int = -20, kmax: int = 20,
+                 unit_norm: bool = True) -> torch.Tensor:
+    """Vector i of a basis of N(0,1) * 2^k values (k uniform in [kmin, kmax] per 32-value block),
+    drawn from its own stream (seed, i) so that a large basis can be generated one vector at a
+    time; scaled to unit 2-norm like a Krylov vector when unit_norm is set."""
+    g = _gen(seed * 1000003 + i, device)
+    nb = (n + 31) // 32
+    x = torch.randn(n, generator=g, device=device, dtype=torch.float64)
+    k = torch.randint(kmin, kmax + 1, (nb,), generator=g, device=device, dtype=torch.int64)
+    x = x * torch.pow(2.0, k.to(torch.float64)).repeat_interleave(32)[:n]
+    if unit_norm:
+        x = x / torch.linalg.vector_norm(x)
+    return x
+
+
 def special_values(device="cpu") -> torch.Tensor:
     """Hand-picked edge values: signed zeros, subnormals, the normal-range boundary, powers of
     two, values that straddle exponents, the largest finite values."""
