@@ -87,13 +87,21 @@ def test_gmres_c1_parity(cbg, orc, c1_inverse_norm, fmt, l):
     res_g = np.linalg.norm(b - orc.spmv(rp, col, vals, xg))
     res_o = np.linalg.norm(b - orc.spmv(rp, col, vals, ref.x))
     assert res_g / np.linalg.norm(b) <= 1.0000001e-10
-    assert abs(r.iters - ref.iters) <= max(1, 0.02 * ref.iters), (r.iters, ref.iters)
     dx = np.linalg.norm(xg - ref.x) / np.linalg.norm(ref.x)
     if fmt in ("fp16", "bf16"):
-        # 11- and 8-bit bases amplify rounding-order differences, so the GPU and oracle iterates
-        # part ways; both solutions still lie within ||A^-1|| (||r_gpu|| + ||r_oracle||) of each other.
+        # 11- and 8-bit bases amplify rounding-order differences: the oracle's own iteration count
+        # moves by up to ~10% when 8 entries of b move by one ulp. The GPU's count must fall in that
+        # band (+-2%), and both solutions lie within ||A^-1|| (||r_gpu|| + ||r_oracle||) of each other.
+        band = [ref.iters]
+        for s in range(1, 24):
+            bb = b.copy()
+            idx = np.random.default_rng(s).integers(0, A.n, 8)
+            bb[idx] = np.nextafter(bb[idx], np.inf)
+            band.append(orc.gmres(rp, col, vals, bb, restart=50, tol=1e-10, fmt=orc.FORMAT_NAMES[fmt], l=l).iters)
+        assert 0.98 * min(band) <= r.iters <= 1.02 * max(band), (r.iters, min(band), max(band))
         assert np.linalg.norm(xg - ref.x) <= 1.01 * c1_inverse_norm * (res_g + res_o)
     else:
+        assert abs(r.iters - ref.iters) <= max(1, 0.02 * ref.iters), (r.iters, ref.iters)
         assert dx <= 1e-8, dx
 
 
