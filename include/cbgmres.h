@@ -111,6 +111,20 @@ size_t cbg_basis_work_bytes(int64_t n, int32_t nvec);
 int cbg_basis_dot(const cbg_basis* basis, int32_t nvec, const double* d_w, double* d_h, void* d_work,
                   size_t work_bytes, void* stream);
 
+/* The same dot product as cbg_basis_dot for callers that cannot allocate device memory: a plugin
+ * whose host application has reserved all device memory in its own pool, or a latency-critical
+ * path that must not call cudaMalloc (which can synchronise the whole device). The paper has no
+ * counterpart; this is a convenience of the library. It takes no work buffer and allocates nothing:
+ * its partial sums live in a fixed 1 MiB array in device memory that the library defines, which
+ * every GPU that loads the library holds until the process exits.
+ *   - nvec must be at most 128; larger values return CBG_ERR_INVALID_ARG with nothing enqueued.
+ *   - The first call on a device looks up the array's device address (cudaGetSymbolAddress) with
+ *     that device current; make that first call before any stream capture on the device.
+ *   - Every call on a device uses the same array. Calls whose kernels overlap on the GPU (for
+ *     example on two streams at once) race and produce wrong results; order them on one stream.
+ * Other arguments, results and the error bound are those of cbg_basis_dot. */
+int cbg_basis_dot_noalloc(const cbg_basis* basis, int32_t nvec, const double* d_w, double* d_h, void* stream);
+
 /* d_w[k] -= sum_i vhat_i[k] * d_h[i] over i in [0, nvec): the update w := w - V_j h of Fig. 1
  * step 5 (highlighted). The sum over i is exact in integer arithmetic for FRSZ2 (h scaled per
  * block to a 54-bit fixed point), FP64 otherwise. If d_norm2 is not NULL it receives ||w||^2 after

@@ -23,7 +23,8 @@ ERR_NOT_CONVERGED = -5
 
 # Symbols declared in include/cbgmres.h (checked by the CPU tests).
 EXPORTS = ["cbg_frsz2_bytes", "cbg_frsz2_compress", "cbg_frsz2_decompress", "cbg_basis_layout", "cbg_basis_store",
-           "cbg_basis_load", "cbg_basis_work_bytes", "cbg_basis_dot", "cbg_basis_update", "cbg_csr_validate",
+           "cbg_basis_load", "cbg_basis_work_bytes", "cbg_basis_dot", "cbg_basis_dot_noalloc", "cbg_basis_update",
+           "cbg_csr_validate",
            "cbg_spmv_work_bytes", "cbg_spmv", "cbg_opts_default", "cbgmres_workspace_bytes", "cbgmres_create",
            "cbgmres_solve", "cbgmres_start", "cbgmres_advance", "cbgmres_finish", "cbgmres_history",
            "cbgmres_destroy", "cbg_last_error", "cbg_version"]
@@ -84,6 +85,7 @@ def load(path: str | None = None):
         "cbg_basis_load": (c_int, [ctypes.POINTER(Basis), i32, P, P]),
         "cbg_basis_work_bytes": (sz, [i64, i32]),
         "cbg_basis_dot": (c_int, [ctypes.POINTER(Basis), i32, P, P, P, sz, P]),
+        "cbg_basis_dot_noalloc": (c_int, [ctypes.POINTER(Basis), i32, P, P, P]),
         "cbg_basis_update": (c_int, [ctypes.POINTER(Basis), i32, P, P, P, P, sz, P]),
         "cbg_csr_validate": (c_int, [i32, i64, P, P, P]),
         "cbg_spmv_work_bytes": (sz, [i32]),

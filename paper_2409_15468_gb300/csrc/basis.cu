@@ -861,6 +861,64 @@ int launch_basis_dot(const BasisView& B, int nvec, const double* w, double* out,
   return CBG_OK;
 }
 
+// The basis dot with the grid limited to max_grid CTAs, for callers whose partial-sum buffer has a
+// fixed capacity (max_grid * nvec doubles).
+int launch_basis_dot_capped(const BasisView& B, int nvec, const double* w, double* out, double* partials,
+                            unsigned int* counter, int* err, int max_grid, cudaStream_t stream) {
+  if (nvec <= 0 || B.n <= 0) return CBG_OK;
+  const Gate gate{nullptr, nullptr};
+  const void* fn;
+  size_t smem;
+  int threads;
+  int64_t units, per;
+  if (B.fmt == CBG_FRSZ2) {
+    threads = 128;
+    units = (B.n + 31) / 32;
+    per = 16;
+    switch (B.l) {
+      case 32: fn = fnp(k_dot_frsz2<32>); smem = DotCfg<32>::smem_bytes(nvec); break;
+      case 21: fn = fnp(k_dot_frsz2<21>); smem = DotCfg<21>::smem_bytes(nvec); break;
+      case 16: fn = fnp(k_dot_frsz2<16>); smem = DotCfg<16>::smem_bytes(nvec); break;
+      default: return CBG_ERR_INVALID_ARG;
+    }
+  } else {
+    threads = CastCfg::kThreads;
+    units = B.n;
+    per = 4096;
+    smem = CastCfg::dot_smem(nvec);
+    switch (B.fmt) {
+      case CBG_FP64: fn = fnp(k_dot_cast<CBG_FP64>); break;
+      case CBG_FP32: fn = fnp(k_dot_cast<CBG_FP32>); break;
+      case CBG_FP16: fn = fnp(k_dot_cast<CBG_FP16>); break;
+      case CBG_BF16: fn = fnp(k_dot_cast<CBG_BF16>); break;
+      default: return CBG_ERR_INVALID_ARG;
+    }
+  }
+  int st = ensure_smem(fn, smem);
+  if (st) return st;
+  int grid;
+  st = grid_for(fn, threads, smem, units, per, &grid);
+  if (st) return st;
+  if (grid > max_grid) grid = max_grid;
+  if (B.fmt == CBG_FRSZ2) {
+    switch (B.l) {
+      case 32: k_dot_frsz2<32><<<grid, threads, smem, stream>>>(B, nvec, w, out, partials, counter, err, gate); break;
+      case 21: k_dot_frsz2<21><<<grid, threads, smem, stream>>>(B, nvec, w, out, partials, counter, err, gate); break;
+      default: k_dot_frsz2<16><<<grid, threads, smem, stream>>>(B, nvec, w, out, partials, counter, err, gate); break;
+    }
+  } else {
+    switch (B.fmt) {
+      case CBG_FP64: k_dot_cast<CBG_FP64><<<grid, threads, smem, stream>>>(B, nvec, w, out, partials, counter, gate); break;
+      case CBG_FP32: k_dot_cast<CBG_FP32><<<grid, threads, smem, stream>>>(B, nvec, w, out, partials, counter, gate); break;
+      case CBG_FP16: k_dot_cast<CBG_FP16><<<grid, threads, smem, stream>>>(B, nvec, w, out, partials, counter, gate); break;
+      default: k_dot_cast<CBG_BF16><<<grid, threads, smem, stream>>>(B, nvec, w, out, partials, counter, gate); break;
+    }
+  }
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(e, "basis dot launch");
+  return CBG_OK;
+}
+
 int launch_basis_update(const BasisView& B, int nvec, const int* nvec_dev, const double* h, int negate, double* w,
                         double* partials, unsigned int* counter, int* err, const NormEpilogue& epi, const Gate& gate,
                         cudaStream_t stream) {

@@ -57,6 +57,9 @@ __device__ __forceinline__ void norm_epilogue(const NormEpilogue& e, double norm
 // out[i] = <vhat_i, w> for i < nvec. partials: kMaxGrid * nvec doubles. *counter must be 0.
 int launch_basis_dot(const BasisView& B, int nvec, const double* w, double* out, double* partials,
                      unsigned int* counter, int* err, const Gate& gate, cudaStream_t stream);
+// The same with at most max_grid CTAs (partials: max_grid * nvec doubles).
+int launch_basis_dot_capped(const BasisView& B, int nvec, const double* w, double* out, double* partials,
+                            unsigned int* counter, int* err, int max_grid, cudaStream_t stream);
 // w -= sum_i vhat_i h_i (h negated when `negate`), nvec from *nvec_dev when not null (then
 // nvec is the upper bound used to size shared memory). ||w||^2 goes to the epilogue.
 int launch_basis_update(const BasisView& B, int nvec, const int* nvec_dev, const double* h, int negate, double* w,
