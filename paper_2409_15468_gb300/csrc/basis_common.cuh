@@ -1,0 +1,70 @@
+// Device helpers shared by the basis kernels (FRSZ2 and cast formats).
+#pragma once
+
+#include "common.cuh"
+#include "kernels.cuh"
+
+namespace cbg {
+
+// Range of 32-value blocks handled by CTA c of G: balanced, starting at multiples of 4 blocks so
+// that every bulk copy starts 16-byte aligned.
+__device__ __forceinline__ void cta_block_range(int64_t nb, int G, int c, int64_t* b0, int64_t* b1) {
+  const int64_t nu = (nb + 3) / 4;
+  const int64_t u0 = nu * c / G, u1 = nu * (c + 1) / G;
+  *b0 = u0 * 4 < nb ? u0 * 4 : nb;
+  *b1 = u1 * 4 < nb ? u1 * 4 : nb;
+}
+
+__device__ __forceinline__ bool gate_skip(const Gate& g) {
+  if (g.stop && *(volatile const int*)g.stop) return true;
+  if (g.need && !*(volatile const int*)g.need) return true;
+  return false;
+}
+
+__device__ __forceinline__ int flag_read(const int* f) { return *(volatile const int*)f; }
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
+}
+
+// acc += a * b with a 32x32 -> 64-bit signed multiply-add (one mad.wide.s32).
+__device__ __forceinline__ void mac_wide(long long& acc, int32_t a, int32_t b) {
+  asm("mad.wide.s32 %0, %1, %2, %0;" : "+l"(acc) : "r"(a), "r"(b));
+}
+
+// Prefetch `bytes` (multiple of 16, 16-byte aligned) of global memory into L2 with the bulk-copy unit.
+__device__ __forceinline__ void bulk_prefetch_l2(const void* p, uint32_t bytes) {
+  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
+}
+
+// Sign-magnitude FRSZ2 code (sign bit NB-1, magnitude below it) to a two's complement integer.
+template <int NB>
+__device__ __forceinline__ int32_t code_to_int(uint32_t c) {
+  const int32_t m = static_cast<int32_t>(c << (32 - NB)) >> 31;  // 0 or -1 from the sign bit
+  return static_cast<int32_t>((c & ((1u << (NB - 1)) - 1u)) ^ static_cast<uint32_t>(m)) - m;
+}
+
+__device__ __forceinline__ int eff_exp(double x) {
+  const int e = static_cast<int>((static_cast<uint64_t>(__double_as_longlong(x)) >> 52) & 0x7FF);
+  return e > 1 ? e : 1;
+}
+
+// x rounded to the block fixed point with exponent ew (the block's largest effective IEEE
+// exponent): W = round(|x| 2^{1075-ew}) with sign, |W| < 2^53, split as W1 * 2^27 + W0 with
+// W0 in [0, 2^27) and |W1| <= 2^26.
+__device__ __forceinline__ void to_block_fixed(double x, int ew, int32_t& w1, int32_t& w0) {
+  const uint64_t u = static_cast<uint64_t>(__double_as_longlong(x));
+  const int e = static_cast<int>((u >> 52) & 0x7FF);
+  uint64_t m = u & ((1ull << 52) - 1);
+  if (e) m |= 1ull << 52;
+  const int sh = ew - (e > 1 ? e : 1);
+  uint64_t mag;
+  if (sh == 0) mag = m;
+  else if (sh < 64) mag = ((m >> (sh - 1)) + 1) >> 1;  // round half up
+  else mag = 0;
+  const int64_t W = (u >> 63) ? -static_cast<int64_t>(mag) : static_cast<int64_t>(mag);
+  w1 = static_cast<int32_t>(W >> 27);
+  w0 = static_cast<int32_t>(W & ((1ll << 27) - 1));
+}
+
+}  // namespace cbg

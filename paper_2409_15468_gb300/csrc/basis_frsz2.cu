@@ -1,0 +1,687 @@
+// FRSZ2 basis kernels: the Gram-Schmidt projections h = V^T w and the update w -= V h of Fig. 1
+// step 5 (and steps 8 and 17), decoding the stored FRSZ2 codes in registers.
+//
+// An FRSZ2 block is block fixed point (Eq. 2): value k of block b of vector i is s_{i,k} 2^{q_{i,b}}
+// with s a signed integer of l-1 magnitude bits. GB300 issues FP64 at ~1.9 operations per clock per
+// SM (conversions to FP64 included) against ~57 32x32->64 integer multiply-adds, so both kernels do
+// the per-element work as exact integer arithmetic and touch FP64 once per block or per element:
+//
+//   dot     sum_{k in b} s_{i,k} W_k, W a 54-bit block-fixed-point copy of w (rounded to nearest
+//           against the block's largest exponent), is exact in two 64-bit accumulators; the sum
+//           (at most l+57 bits) is rounded to 2^(l-5) units in integer arithmetic and converted
+//           once per (vector, block), then summed in FP64 (per warp, per CTA, across CTAs in a
+//           fixed order).
+//   update  sum_i s_{i,k} G_{i,b}, G the 54-bit fixed point of h_i 2^{q_{i,b}} against the
+//           block's largest term over a group of at most 32 vectors, is exact in two 64-bit
+//           accumulators (27-bit pieces of G) and converted once per element and group.
+//
+// The basis is streamed with 1D bulk copies (TMA) into a ring of shared-memory stages. Each stage
+// has a "full" mbarrier (the copy's transaction count) and an "empty" mbarrier (one arrival per
+// warp); thread 0 refills the stage released one iteration earlier, so warps never wait on each
+// other inside the vector loop. Every wait is bounded (globaltimer); on expiry the kernel records
+// kDevErrTimeout, waits (bounded) for its own copies in flight and returns.
+#include "basis_common.cuh"
+
+namespace cbg {
+
+// ================================================================================================
+// dot: one thread per 32-value block, 128 blocks per tile, every vector of the basis per tile
+// ================================================================================================
+
+template <int L>
+struct FDot {
+  static constexpr int kThreads = 128;
+  static constexpr int kWarps = 4;
+  static constexpr int kStages = (L == 32) ? 3 : 4;
+  static constexpr int kBatch = 8;       // vectors per per-warp reduction
+  static constexpr int kRedStride = 33;  // doubles per batch row (padded against bank conflicts)
+  static constexpr int kCodeBytes = kThreads * L * 4;
+  static constexpr int kStageBytes = kCodeBytes + kThreads * 4;
+  static constexpr int kRedDoubles = kWarps * kBatch * kRedStride;
+  static size_t smem_bytes(int nvec) {
+    return (size_t)kStages * kStageBytes + (size_t)kRedDoubles * 8 + (size_t)kWarps * nvec * 8 +
+           2 * kStages * 8 + 16;
+  }
+};
+
+// Integer dot of one block's codes with the thread's W registers; four independent accumulator
+// chains (even/odd values for each half of W).
+template <int L>
+__device__ __forceinline__ void block_dot(const uint32_t* cw, int t, const int32_t (&W1)[32], const int32_t (&W0)[32],
+                                          long long& a1, long long& a0) {
+  long long a1e = 0, a0e = 0, a1o = 0, a0o = 0;
+  if (L == 32) {
+    // 8 chunks of 16 bytes, visited in an order rotated by t so that the 8 threads of a
+    // shared-memory phase hit distinct banks; W was loaded in the same rotated order.
+    const uint4* c4 = reinterpret_cast<const uint4*>(cw);
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+      const uint4 q = c4[(c + t) & 7];
+      const int32_t s0 = code_to_int<32>(q.x), s1 = code_to_int<32>(q.y);
+      const int32_t s2 = code_to_int<32>(q.z), s3 = code_to_int<32>(q.w);
+      mac_wide(a1e, s0, W1[4 * c + 0]);
+      mac_wide(a0e, s0, W0[4 * c + 0]);
+      mac_wide(a1o, s1, W1[4 * c + 1]);
+      mac_wide(a0o, s1, W0[4 * c + 1]);
+      mac_wide(a1e, s2, W1[4 * c + 2]);
+      mac_wide(a0e, s2, W0[4 * c + 2]);
+      mac_wide(a1o, s3, W1[4 * c + 3]);
+      mac_wide(a0o, s3, W0[4 * c + 3]);
+    }
+  } else if (L == 16) {
+    // 4 chunks of 8 codes, rotated by t/2 (two threads share a 128-byte bank row)
+    const uint4* c4 = reinterpret_cast<const uint4*>(cw);
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      const uint4 q = c4[(c + (t >> 1)) & 3];
+      const uint32_t wv[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll
+      for (int h = 0; h < 4; ++h) {
+        const int32_t lo = code_to_int<16>(wv[h] & 0xFFFFu);
+        const int32_t hi = code_to_int<16>(wv[h] >> 16);
+        mac_wide(a1e, lo, W1[8 * c + 2 * h]);
+        mac_wide(a0e, lo, W0[8 * c + 2 * h]);
+        mac_wide(a1o, hi, W1[8 * c + 2 * h + 1]);
+        mac_wide(a0o, hi, W0[8 * c + 2 * h + 1]);
+      }
+    }
+  } else {
+    // 21 words; word i of thread t is in bank (21 t + i) mod 32, distinct across a warp
+    uint32_t wd[22];
+#pragma unroll
+    for (int i = 0; i < 21; ++i) wd[i] = cw[i];
+    wd[21] = 0;
+#pragma unroll
+    for (int k = 0; k < 32; ++k) {
+      const int bit = 21 * k, a = bit >> 5, o = bit & 31;
+      const int32_t s = code_to_int<21>(__funnelshift_r(wd[a], wd[a + 1], o) & 0x1FFFFFu);
+      if (k & 1) {
+        mac_wide(a1o, s, W1[k]);
+        mac_wide(a0o, s, W0[k]);
+      } else {
+        mac_wide(a1e, s, W1[k]);
+        mac_wide(a0e, s, W0[k]);
+      }
+    }
+  }
+  a1 = a1e + a1o;
+  a0 = a0e + a0o;
+}
+
+// Register slot r of the thread's W holds block value w_index(L, t, r) (the order block_dot reads).
+template <int L>
+__device__ __forceinline__ int w_index(int t, int r) {
+  const int c = r >> 2, q = r & 3;
+  if (L == 32) return 4 * ((c + t) & 7) + q;
+  if (L == 16) return 8 * (((c >> 1) + (t >> 1)) & 3) + 4 * (c & 1) + q;
+  return r;
+}
+
+template <int L>
+__global__ void __launch_bounds__(FDot<L>::kThreads) k_dot_frsz2(BasisView B, int nvec, const double* __restrict__ w,
+                                                                 double* __restrict__ out,
+                                                                 double* __restrict__ partials,
+                                                                 unsigned int* counter, int* err, Gate gate) {
+  using C = FDot<L>;
+  constexpr int T = C::kThreads, S = C::kStages;
+  if (gate_skip(gate)) return;
+  extern __shared__ __align__(128) uint8_t smem[];
+  uint8_t* stages = smem;
+  double* red = reinterpret_cast<double*>(smem + S * C::kStageBytes);
+  double* hpart = red + C::kRedDoubles;
+  uint64_t* full = reinterpret_cast<uint64_t*>(hpart + C::kWarps * nvec);
+  uint64_t* empty = full + S;
+  int* flags = reinterpret_cast<int*>(empty + S);  // [0] abort, [1] last-CTA flag
+
+  const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
+  const int64_t nb = (B.n + 31) / 32;
+  int64_t b0, b1;
+  cta_block_range(nb, gridDim.x, blockIdx.x, &b0, &b1);
+  const int ntiles = static_cast<int>((b1 - b0 + T - 1) / T);
+  const int total = ntiles * nvec;
+
+  for (int i = t; i < C::kWarps * nvec; i += T) hpart[i] = 0.0;
+  if (t == 0) {
+    for (int s = 0; s < S; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], C::kWarps);
+    }
+    fence_mbar_init();
+    flags[0] = 0;
+  }
+  __syncthreads();
+
+  auto issue = [&](int p) {
+    const int tile = p / nvec, vec = p - tile * nvec, s = p % S;
+    const int64_t tb0 = b0 + (int64_t)tile * T;
+    const int nbt = static_cast<int>(min((int64_t)T, b1 - tb0));
+    const uint32_t cbytes = static_cast<uint32_t>((nbt * L * 4 + 15) & ~15);
+    const uint32_t ebytes = static_cast<uint32_t>((nbt * 4 + 15) & ~15);
+    uint8_t* dst = stages + s * C::kStageBytes;
+    fence_proxy_async_smem();
+    mbar_arrive_expect_tx(&full[s], cbytes + ebytes);
+    bulk_g2s(dst, B.vals + (int64_t)vec * B.vstride + tb0 * L * 4, cbytes, &full[s]);
+    bulk_g2s(dst + C::kCodeBytes, reinterpret_cast<const uint8_t*>(B.exps) + (int64_t)vec * B.estride + tb0 * 4,
+             ebytes, &full[s]);
+  };
+  int issued = 0;  // thread 0 only
+  if (t == 0) {
+    for (; issued < S && issued < total; ++issued) issue(issued);
+  }
+
+  double* myred = red + warp * C::kBatch * C::kRedStride;
+  double* myh = hpart + warp * nvec;
+  int it = 0;
+  bool aborted = false;
+  for (int tile = 0; tile < ntiles && !aborted; ++tile) {
+    const int64_t b = b0 + (int64_t)tile * T + t;
+    const bool active = b < b1;
+    if (t == 0 && tile + 1 < ntiles) {  // the next tile's w: in L2 by the time it is needed
+      const int64_t nb0 = b0 + (int64_t)(tile + 1) * T;
+      const int64_t vals = min((int64_t)T, b1 - nb0) * 32;
+      const int64_t bytes = min(vals, B.n - nb0 * 32) * 8;
+      if (bytes >= 16) bulk_prefetch_l2(w + nb0 * 32, static_cast<uint32_t>(bytes & ~15ll));
+    }
+    // 54-bit block-fixed-point copy of this thread's 32 values of w, kept in registers
+    int32_t W1[32], W0[32];
+    int ew = 1;
+    if (active) {
+      const double* wb = w + b * 32;
+      const int64_t rem = B.n - b * 32;
+      if (rem >= 32) {
+        const double2* w2 = reinterpret_cast<const double2*>(wb);
+#pragma unroll
+        for (int k = 0; k < 16; ++k) {
+          const double2 v = __ldg(w2 + k);
+          ew = max(ew, max(eff_exp(v.x), eff_exp(v.y)));
+        }
+#pragma unroll
+        for (int r = 0; r < 32; r += 2) {
+          const double2 v = __ldg(reinterpret_cast<const double2*>(wb + w_index<L>(t, r)));
+          to_block_fixed(v.x, ew, W1[r], W0[r]);
+          to_block_fixed(v.y, ew, W1[r + 1], W0[r + 1]);
+        }
+      } else {
+#pragma unroll
+        for (int k = 0; k < 32; ++k) ew = max(ew, eff_exp(k < rem ? wb[k] : 0.0));
+#pragma unroll
+        for (int r = 0; r < 32; ++r) {
+          const int k = w_index<L>(t, r);
+          to_block_fixed(k < rem ? wb[k] : 0.0, ew, W1[r], W0[r]);
+        }
+      }
+    } else {
+#pragma unroll
+      for (int r = 0; r < 32; ++r) W1[r] = W0[r] = 0;
+    }
+    for (int vec = 0; vec < nvec; ++vec, ++it) {
+      const int s = it % S;
+      // lagged refill: the stage released by every warp in the previous iteration
+      if (t == 0 && it >= 1 && issued < total) {
+        const int sp = (it - 1) % S;
+        if (mbar_wait_bounded(&empty[sp], static_cast<uint32_t>(((it - 1) / S) & 1))) {
+          issue(issued);
+          ++issued;
+        } else {
+          flags[0] = 1;
+          atomicOr(err, kDevErrTimeout);
+        }
+      }
+      bool ok = !flag_read(&flags[0]) && mbar_wait_bounded(&full[s], static_cast<uint32_t>((it / S) & 1));
+      if (!ok && !flag_read(&flags[0])) {
+        flags[0] = 1;
+        atomicOr(err, kDevErrTimeout);
+      }
+      double hp = 0.0;
+      if (active && ok) {
+        const uint8_t* st = stages + s * C::kStageBytes;
+        const uint32_t e = reinterpret_cast<const uint32_t*>(st + C::kCodeBytes)[t];
+        long long a1, a0;
+        block_dot<L>(reinterpret_cast<const uint32_t*>(st) + t * L, t, W1, W0, a1, a0);
+        // sum = (a1 2^27 + a0) 2^x with x = Ebar + Ew - 2096 - l, |a1 2^27 + a0| < 2^(l+57).
+        // Rounded to 2^(l-5) units it fits in 63 bits; the rounding error, at most 2^(l-6) units,
+        // is a quarter of the bound 2^-54 max|w| sum|vhat| of a block whose maxima are normal.
+        const long long th = (a1 << (32 - L)) + ((a0 + (1ll << (L - 6))) >> (L - 5));
+        const int x = (e > 1 ? static_cast<int>(e) : 1) + ew - 2096 - L;
+        hp = scale_pow2(static_cast<double>(th), x + L - 5);
+      }
+      myred[(vec % C::kBatch) * C::kRedStride + lane] = hp;
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&empty[s]);
+      if (vec % C::kBatch == C::kBatch - 1 || vec == nvec - 1) {
+        const int first = vec - (vec % C::kBatch), cnt = vec - first + 1;
+        const int v = lane & 7, part = lane >> 3;
+        double sacc = 0.0;
+        if (v < cnt) {
+#pragma unroll
+          for (int i = 0; i < 8; ++i) sacc += myred[v * C::kRedStride + part * 8 + i];
+        }
+        sacc += __shfl_xor_sync(0xffffffffu, sacc, 8);
+        sacc += __shfl_xor_sync(0xffffffffu, sacc, 16);
+        if (part == 0 && v < cnt) myh[first + v] += sacc;
+        __syncwarp();
+      }
+      if (flag_read(&flags[0])) {
+        aborted = true;
+        break;
+      }
+    }
+  }
+  __syncthreads();
+  if (flag_read(&flags[0])) {
+    // wait (bounded) for this CTA's copies still in flight, then leave without a result
+    if (t == 0) {
+      for (int p = max(0, issued - S); p < issued; ++p)
+        mbar_wait_bounded(&full[p % S], static_cast<uint32_t>((p / S) & 1));
+    }
+    return;
+  }
+  for (int v = t; v < nvec; v += T) {
+    double sacc = 0.0;
+#pragma unroll
+    for (int i = 0; i < C::kWarps; ++i) sacc += hpart[i * nvec + v];
+    partials[(size_t)blockIdx.x * nvec + v] = sacc;
+  }
+  if (arrive_last(counter, gridDim.x, &flags[1])) {
+    for (int v = warp; v < nvec; v += C::kWarps) {
+      const double sum = warp_sum_strided(partials + v, gridDim.x, nvec);
+      if (lane == 0) out[v] = sum;
+    }
+    if (t == 0) *counter = 0;
+  }
+}
+
+// ================================================================================================
+// update: 16 consecutive values per thread, 2 threads per block, 64 blocks per tile, vectors in
+// groups of at most 32 (the exact integer sums are per group)
+// ================================================================================================
+
+template <int L>
+struct FUpd {
+  static constexpr int kThreads = 128;
+  static constexpr int kWarps = 4;
+  static constexpr int kBlocks = 64;
+  static constexpr int kStages = 5;
+  static constexpr int kGroup = 32;
+  static constexpr int kStageBytes = kBlocks * L * 4;
+  // dynamic smem: stages | coefficient table [kGroup][kBlocks] (int2) | exponent words of one group
+  //               [kGroup][kBlocks] | hinfo[nvec_max] | red[kWarps] | full, empty, exps barriers | flags
+  static size_t smem_bytes(int nvec_max) {
+    return (size_t)kStages * kStageBytes + (size_t)kGroup * kBlocks * 8 + (size_t)kGroup * kBlocks * 4 +
+           (size_t)nvec_max * 16 + kWarps * 8 + (2 * kStages + 2) * 8 + 16;
+  }
+};
+
+struct HInfo {  // a coefficient h_i as sign, 53-bit integer significand and effective exponent
+  unsigned long long mant;
+  int eff;
+  int neg;
+};
+
+// The 16 codes of this thread (values 16 h .. 16 h + 15 of block t/2, h = t%2) from a stage, in
+// register slots whose order is rotated by the thread index so that the threads of a shared-memory
+// phase hit distinct banks. slot_pos gives the value each slot holds.
+template <int L>
+__device__ __forceinline__ void load_codes16(const uint32_t* st, int t, uint32_t (&c)[16]) {
+  if (L == 32) {
+    const uint4* p = reinterpret_cast<const uint4*>(st) + 4 * t;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const uint4 a = p[(j + (t >> 1)) & 3];
+      c[4 * j] = a.x; c[4 * j + 1] = a.y; c[4 * j + 2] = a.z; c[4 * j + 3] = a.w;
+    }
+  } else if (L == 16) {
+    const uint4* p = reinterpret_cast<const uint4*>(st) + 2 * t;
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+      const uint4 a = p[(j + (t >> 2)) & 1];
+      const uint32_t wv[4] = {a.x, a.y, a.z, a.w};
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        c[8 * j + 2 * i] = wv[i] & 0xFFFFu;
+        c[8 * j + 2 * i + 1] = wv[i] >> 16;
+      }
+    }
+  } else {
+    // codes 16 h .. 16 h + 15 of a block occupy stream bits [336 h, 336 h + 336)
+    const int blk = t >> 1, h = t & 1;
+    const uint32_t* bw = st + blk * 21;
+    const int wbase = h ? 10 : 0, o = h ? 16 : 0;
+    uint32_t raw[12];
+#pragma unroll
+    for (int i = 0; i < 12; ++i) raw[i] = (wbase + i < 21) ? bw[wbase + i] : 0u;
+    uint32_t al[11];
+#pragma unroll
+    for (int i = 0; i < 11; ++i) al[i] = __funnelshift_r(raw[i], raw[i + 1], o);
+#pragma unroll
+    for (int k = 0; k < 16; ++k) {
+      const int bit = 21 * k, a = bit >> 5, oo = bit & 31;
+      c[k] = __funnelshift_r(al[a], al[a + 1], oo) & 0x1FFFFFu;
+    }
+  }
+}
+
+template <int L>
+__device__ __forceinline__ int slot_pos(int t, int k) {
+  if (L == 32) return 4 * (((k >> 2) + (t >> 1)) & 3) + (k & 3);
+  if (L == 16) return 8 * (((k >> 3) + (t >> 2)) & 1) + (k & 7);
+  return k;
+}
+
+template <int L>
+__global__ void __launch_bounds__(FUpd<L>::kThreads) k_update_frsz2(BasisView B, int nvec_arg, const int* nvec_dev,
+                                                                    const double* __restrict__ hcoef, int negate,
+                                                                    double* __restrict__ w,
+                                                                    double* __restrict__ partials,
+                                                                    unsigned int* counter, int* err, NormEpilogue epi,
+                                                                    Gate gate) {
+  using C = FUpd<L>;
+  constexpr int T = C::kThreads, NBT = C::kBlocks, G = C::kGroup, S = C::kStages;
+  if (gate_skip(gate)) return;
+  const int nvec = nvec_dev ? *(volatile const int*)nvec_dev : nvec_arg;
+  const int nvec_cap = nvec_dev ? nvec_arg : nvec;
+  extern __shared__ __align__(128) uint8_t smem[];
+  uint8_t* stages = smem;
+  int2* gam = reinterpret_cast<int2*>(smem + S * C::kStageBytes);
+  uint32_t* exq = reinterpret_cast<uint32_t*>(gam + G * NBT);
+  HInfo* hinfo = reinterpret_cast<HInfo*>(exq + G * NBT);
+  double* red = reinterpret_cast<double*>(hinfo + nvec_cap);
+  uint64_t* full = reinterpret_cast<uint64_t*>(red + C::kWarps);
+  uint64_t* empty = full + S;
+  uint64_t* ebar = empty + S;  // exponent words of the next group ([1] unused, keeps alignment)
+  int* flags = reinterpret_cast<int*>(ebar + 2);
+
+  const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
+  const int blk = t >> 1, hq = t & 1;
+  const int64_t nb = (B.n + 31) / 32;
+  int64_t b0, b1;
+  cta_block_range(nb, gridDim.x, blockIdx.x, &b0, &b1);
+  const int ntiles = static_cast<int>((b1 - b0 + NBT - 1) / NBT);
+  const int total = ntiles * nvec;
+
+  for (int i = t; i < nvec; i += T) {
+    const double h = negate ? -hcoef[i] : hcoef[i];
+    const uint64_t u = static_cast<uint64_t>(__double_as_longlong(h));
+    const int e = static_cast<int>((u >> 52) & 0x7FF);
+    HInfo hi;
+    hi.mant = (u & ((1ull << 52) - 1)) | (e ? (1ull << 52) : 0ull);
+    hi.eff = e > 1 ? e : 1;
+    hi.neg = static_cast<int>(u >> 63);
+    hinfo[i] = hi;
+  }
+  if (t == 0) {
+    for (int s = 0; s < S; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], C::kWarps);
+    }
+    mbar_init(&ebar[0], 1);
+    fence_mbar_init();
+    flags[0] = 0;
+  }
+  __syncthreads();
+
+  auto issue = [&](int p) {
+    const int tile = p / nvec, vec = p - tile * nvec, s = p % S;
+    const int64_t tb0 = b0 + (int64_t)tile * NBT;
+    const int nbt = static_cast<int>(min((int64_t)NBT, b1 - tb0));
+    const uint32_t cbytes = static_cast<uint32_t>((nbt * L * 4 + 15) & ~15);
+    fence_proxy_async_smem();
+    mbar_arrive_expect_tx(&full[s], cbytes);
+    bulk_g2s(stages + s * C::kStageBytes, B.vals + (int64_t)vec * B.vstride + tb0 * L * 4, cbytes, &full[s]);
+  };
+  // Exponent words of group [g0, g0 + G) for tile `tile`, one bulk copy per vector into exq[v][*],
+  // issued by the 32 lanes of warp 0 (lane 0 first posts the expected byte count).
+  auto issue_exps = [&](int tile, int g0) {
+    const int64_t tb0 = b0 + (int64_t)tile * NBT;
+    const int nbt = static_cast<int>(min((int64_t)NBT, b1 - tb0));
+    const int gn = min(G, nvec - g0);
+    const uint32_t ebytes = static_cast<uint32_t>((nbt * 4 + 15) & ~15);
+    if (lane == 0) {
+      fence_proxy_async_smem();
+      mbar_arrive_expect_tx(&ebar[0], ebytes * gn);
+    }
+    __syncwarp();
+    for (int v = lane; v < gn; v += 32)
+      bulk_g2s(exq + v * NBT, reinterpret_cast<const uint8_t*>(B.exps) + (int64_t)(g0 + v) * B.estride + tb0 * 4,
+               ebytes, &ebar[0]);
+  };
+  int issued = 0, eissued = 0;  // warp 0: code copies (thread 0) and exponent-group copies issued
+  if (warp == 0 && ntiles > 0 && nvec > 0) {
+    issue_exps(0, 0);
+    ++eissued;
+  }
+  if (t == 0) {
+    for (; issued < S && issued < total; ++issued) issue(issued);
+  }
+  int egroups = 0;  // exponent copies consumed so far (phase of ebar)
+
+  double nrm = 0.0;
+  int it = 0;
+  bool aborted = false;
+  for (int tile = 0; tile < ntiles && !aborted; ++tile) {
+    const int64_t tb0 = b0 + (int64_t)tile * NBT;
+    const int nbt = static_cast<int>(min((int64_t)NBT, b1 - tb0));
+    const bool active = blk < nbt;
+    const int64_t k0 = (tb0 + blk) * 32 + hq * 16;  // first of this thread's 16 values
+    double dacc[16];
+#pragma unroll
+    for (int k = 0; k < 16; ++k) dacc[k] = 0.0;
+    for (int g0 = 0; g0 < nvec; g0 += G) {
+      const int gn = min(G, nvec - g0);
+      __syncthreads();  // the previous group's coefficient table is no longer read
+      if (flag_read(&flags[0])) {  // read after a barrier: the same decision in every thread
+        aborted = true;
+        break;
+      }
+      const bool eok = mbar_wait_bounded(&ebar[0], static_cast<uint32_t>(egroups & 1));
+      ++egroups;
+      if (!eok) {
+        flags[0] = 1;
+        atomicOr(err, kDevErrTimeout);
+      }
+      // rexp = max over the group of (Eh_i + Ebar_{i,b}): exponent of the block's largest term;
+      // the 2 threads of a block split the group's vectors and combine with a shuffle.
+      uint32_t ev[G / 2];
+      int r = 0;
+#pragma unroll
+      for (int kk = 0; kk < G / 2; ++kk) {
+        const int v = hq + 2 * kk;
+        const uint32_t e = (v < gn && active && eok) ? exq[v * NBT + blk] : 0u;
+        ev[kk] = e;
+        if (v < gn) r = max(r, hinfo[g0 + v].eff + (e > 1 ? static_cast<int>(e) : 1));
+      }
+      r = max(r, __shfl_xor_sync(0xffffffffu, r, 1));
+      // G_{i,b} = round(Mh_i 2^{Eh_i + Ebar_{i,b} - rexp}) with sign, |G| < 2^53, as
+      // G0 = G mod 2^27 in [0, 2^27) and G1 = floor(G / 2^27) in [-2^26, 2^26)
+#pragma unroll
+      for (int kk = 0; kk < G / 2; ++kk) {
+        const int v = hq + 2 * kk;
+        if (v < gn) {
+          const HInfo hi = hinfo[g0 + v];
+          const uint32_t e = ev[kk];
+          const int sh = r - (hi.eff + (e > 1 ? static_cast<int>(e) : 1));
+          uint64_t mag;
+          if (sh == 0) mag = hi.mant;
+          else if (sh < 64) mag = ((hi.mant >> (sh - 1)) + 1) >> 1;
+          else mag = 0;
+          if (mag >> 53) mag = (1ull << 53) - 1;  // rounding up to 2^53: stay below it
+          const int64_t gm = hi.neg ? -static_cast<int64_t>(mag) : static_cast<int64_t>(mag);
+          gam[v * NBT + blk] = make_int2(static_cast<int32_t>(gm & ((1ll << 27) - 1)), static_cast<int32_t>(gm >> 27));
+        }
+      }
+      __syncthreads();
+      // the exponent words of the next group arrive while this group is processed
+      if (warp == 0 && !flag_read(&flags[0])) {
+        if (g0 + G < nvec) {
+          issue_exps(tile, g0 + G);
+          ++eissued;
+        } else if (tile + 1 < ntiles) {
+          issue_exps(tile + 1, 0);
+          ++eissued;
+        }
+      }
+      long long acc0[16], acc1[16];
+#pragma unroll
+      for (int k = 0; k < 16; ++k) acc0[k] = acc1[k] = 0;
+      for (int v = 0; v < gn; ++v, ++it) {
+        // After an abort the loop keeps running without waiting or computing, so that every thread
+        // reaches the next CTA barrier.
+        const int s = it % S;
+        if (t == 0 && it >= 1 && issued < total && !flag_read(&flags[0])) {
+          const int sp = (it - 1) % S;
+          if (mbar_wait_bounded(&empty[sp], static_cast<uint32_t>(((it - 1) / S) & 1))) {
+            issue(issued);
+            ++issued;
+          } else {
+            flags[0] = 1;
+            atomicOr(err, kDevErrTimeout);
+          }
+        }
+        bool ok = !flag_read(&flags[0]) && mbar_wait_bounded(&full[s], static_cast<uint32_t>((it / S) & 1));
+        if (!ok && !flag_read(&flags[0])) {
+          flags[0] = 1;
+          atomicOr(err, kDevErrTimeout);
+        }
+        if (active && ok) {
+          uint32_t c[16];
+          load_codes16<L>(reinterpret_cast<const uint32_t*>(stages + s * C::kStageBytes), t, c);
+          const int2 gp = gam[v * NBT + blk];
+#pragma unroll
+          for (int k = 0; k < 16; ++k) {
+            const int32_t sv = code_to_int<L>(c[k]);
+            mac_wide(acc0[k], sv, gp.x);
+            mac_wide(acc1[k], sv, gp.y);
+          }
+        }
+        __syncwarp();
+        if (lane == 0 && ok) mbar_arrive(&empty[s]);
+      }
+      if (active && !flag_read(&flags[0])) {
+        // sum_i s G = acc1 2^27 + acc0 exactly (|.| < 2^(l+57)), scale 2^{rexp - 2096 - l}; rounded
+        // to 2^(l-5) units (at most 2^-58 of the block's largest possible term, 2^(l+52) units) and
+        // converted once per value
+        const int x = r - 2096 - 5;
+#pragma unroll
+        for (int k = 0; k < 16; ++k) {
+          const long long th = (acc1[k] << (32 - L)) + ((acc0[k] + (1ll << (L - 6))) >> (L - 5));
+          dacc[k] += scale_pow2(static_cast<double>(th), x);
+        }
+      }
+    }
+    if (aborted || flag_read(&flags[0])) break;
+    if (active) {
+      if (k0 + 16 <= B.n) {
+        // values in slot order: chunks of 4 (l = 32), 8 (l = 16) or 16 (l = 21) consecutive values
+        constexpr int CH = (L == 32) ? 4 : (L == 16 ? 8 : 16);
+#pragma unroll
+        for (int j = 0; j < 16 / CH; ++j) {
+          const int pos = slot_pos<L>(t, j * CH);
+          double2* p = reinterpret_cast<double2*>(w + k0 + pos);
+#pragma unroll
+          for (int i = 0; i < CH / 2; ++i) {
+            double2 v = p[i];
+            v.x -= dacc[j * CH + 2 * i];
+            v.y -= dacc[j * CH + 2 * i + 1];
+            p[i] = v;
+            nrm = fma(v.x, v.x, nrm);
+            nrm = fma(v.y, v.y, nrm);
+          }
+        }
+      } else {
+#pragma unroll
+        for (int k = 0; k < 16; ++k) {
+          const int64_t idx = k0 + slot_pos<L>(t, k);
+          if (idx < B.n) {
+            const double nv = w[idx] - dacc[k];
+            w[idx] = nv;
+            nrm = fma(nv, nv, nrm);
+          }
+        }
+      }
+    }
+  }
+  __syncthreads();
+  if (flag_read(&flags[0])) {
+    if (t == 0) {
+      for (int p = max(0, issued - S); p < issued; ++p)
+        mbar_wait_bounded(&full[p % S], static_cast<uint32_t>((p / S) & 1));
+    }
+    if (warp == 0 && lane == 0 && eissued > egroups) mbar_wait_bounded(&ebar[0], static_cast<uint32_t>(egroups & 1));
+    return;
+  }
+  // ||w||^2: CTA partial, then the last CTA reduces all partials in a fixed order
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) nrm += __shfl_xor_sync(0xffffffffu, nrm, o);
+  if (lane == 0) red[warp] = nrm;
+  __syncthreads();
+  if (t == 0) {
+    double sacc = 0.0;
+    for (int i = 0; i < C::kWarps; ++i) sacc += red[i];
+    partials[blockIdx.x] = sacc;
+  }
+  if (arrive_last(counter, gridDim.x, &flags[1])) {
+    if (warp == 0) {
+      const double sacc = warp_sum_strided(partials, gridDim.x, 1);
+      if (lane == 0) norm_epilogue(epi, sacc, err);
+    }
+    if (t == 0) *counter = 0;
+  }
+}
+
+// ================================================================================================
+// launchers
+// ================================================================================================
+
+namespace {
+template <typename K>
+const void* fnp(K k) {
+  return reinterpret_cast<const void*>(k);
+}
+}  // namespace
+
+int frsz2_dot_launch(const BasisView& B, int nvec, const double* w, double* out, double* partials,
+                     unsigned int* counter, int* err, const Gate& gate, int max_grid, cudaStream_t stream) {
+  const void* fn;
+  size_t smem;
+  switch (B.l) {
+    case 32: fn = fnp(k_dot_frsz2<32>); smem = FDot<32>::smem_bytes(nvec); break;
+    case 21: fn = fnp(k_dot_frsz2<21>); smem = FDot<21>::smem_bytes(nvec); break;
+    case 16: fn = fnp(k_dot_frsz2<16>); smem = FDot<16>::smem_bytes(nvec); break;
+    default: return CBG_ERR_INVALID_ARG;
+  }
+  int grid;
+  int st = basis_launch_config(fn, 128, smem, (B.n + 31) / 32, 16, max_grid, &grid);
+  if (st) return st;
+  switch (B.l) {
+    case 32: k_dot_frsz2<32><<<grid, 128, smem, stream>>>(B, nvec, w, out, partials, counter, err, gate); break;
+    case 21: k_dot_frsz2<21><<<grid, 128, smem, stream>>>(B, nvec, w, out, partials, counter, err, gate); break;
+    default: k_dot_frsz2<16><<<grid, 128, smem, stream>>>(B, nvec, w, out, partials, counter, err, gate); break;
+  }
+  cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? CBG_OK : cuda_fail(e, "frsz2 dot launch");
+}
+
+int frsz2_update_launch(const BasisView& B, int nvec, const int* nvec_dev, const double* h, int negate, double* w,
+                        double* partials, unsigned int* counter, int* err, const NormEpilogue& epi,
+                        const Gate& gate, cudaStream_t stream) {
+  const void* fn;
+  size_t smem;
+  switch (B.l) {
+    case 32: fn = fnp(k_update_frsz2<32>); smem = FUpd<32>::smem_bytes(nvec); break;
+    case 21: fn = fnp(k_update_frsz2<21>); smem = FUpd<21>::smem_bytes(nvec); break;
+    case 16: fn = fnp(k_update_frsz2<16>); smem = FUpd<16>::smem_bytes(nvec); break;
+    default: return CBG_ERR_INVALID_ARG;
+  }
+  int grid;
+  int st = basis_launch_config(fn, 128, smem, (B.n + 31) / 32, 8, kMaxGrid, &grid);
+  if (st) return st;
+  switch (B.l) {
+    case 32: k_update_frsz2<32><<<grid, 128, smem, stream>>>(B, nvec, nvec_dev, h, negate, w, partials, counter, err, epi, gate); break;
+    case 21: k_update_frsz2<21><<<grid, 128, smem, stream>>>(B, nvec, nvec_dev, h, negate, w, partials, counter, err, epi, gate); break;
+    default: k_update_frsz2<16><<<grid, 128, smem, stream>>>(B, nvec, nvec_dev, h, negate, w, partials, counter, err, epi, gate); break;
+  }
+  cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? CBG_OK : cuda_fail(e, "frsz2 update launch");
+}
+
+}  // namespace cbg
