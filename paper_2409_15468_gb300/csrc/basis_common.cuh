@@ -27,9 +27,13 @@ __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
 }
 
-// acc += a * b with a 32x32 -> 64-bit signed multiply-add (one mad.wide.s32).
+// acc += a * b exactly: a 32x32 -> 64-bit signed product, then a 64-bit add. On sm_103a this form
+// executes ~1.5 instructions per product, against ~2.5 for a fused mad.wide.s32 with a 64-bit
+// accumulator (measured with varying operands).
 __device__ __forceinline__ void mac_wide(long long& acc, int32_t a, int32_t b) {
-  asm("mad.wide.s32 %0, %1, %2, %0;" : "+l"(acc) : "r"(a), "r"(b));
+  long long p;
+  asm("mul.wide.s32 %0, %1, %2;" : "=l"(p) : "r"(a), "r"(b));
+  acc += p;
 }
 
 // Prefetch `bytes` (multiple of 16, 16-byte aligned) of global memory into L2 with the bulk-copy unit.

@@ -171,9 +171,14 @@ __global__ void __launch_bounds__(FDot<L>::kThreads) k_dot_frsz2(BasisView B, in
 
   double* myred = red + warp * C::kBatch * C::kRedStride;
   double* myh = hpart + warp * nvec;
-  int it = 0;
-  bool aborted = false;
-  for (int tile = 0; tile < ntiles && !aborted; ++tile) {
+  int s = 0;           // stage of the current vector and the phase parity of its barriers
+  uint32_t ph = 0;
+  int ps = 0;          // stage and parity of the previous vector (refilled by thread 0)
+  uint32_t pph = 0;
+  bool first = true;
+  bool dead = false;   // this warp gave up waiting (warp-uniform); it then runs to the end without waiting
+  bool rfail = false;  // thread 0 gave up waiting for a stage to be released
+  for (int tile = 0; tile < ntiles; ++tile) {
     const int64_t b = b0 + (int64_t)tile * T + t;
     const bool active = b < b1;
     if (t == 0 && tile + 1 < ntiles) {  // the next tile's w: in L2 by the time it is needed
@@ -214,23 +219,28 @@ __global__ void __launch_bounds__(FDot<L>::kThreads) k_dot_frsz2(BasisView B, in
 #pragma unroll
       for (int r = 0; r < 32; ++r) W1[r] = W0[r] = 0;
     }
-    for (int vec = 0; vec < nvec; ++vec, ++it) {
-      const int s = it % S;
+    for (int vec = 0; vec < nvec; ++vec) {
       // lagged refill: the stage released by every warp in the previous iteration
-      if (t == 0 && it >= 1 && issued < total) {
-        const int sp = (it - 1) % S;
-        if (mbar_wait_bounded(&empty[sp], static_cast<uint32_t>(((it - 1) / S) & 1))) {
+      if (t == 0 && !first && issued < total && !rfail && !dead) {
+        if (mbar_wait_bounded(&empty[ps], pph)) {
           issue(issued);
           ++issued;
         } else {
+          rfail = true;
           flags[0] = 1;
           atomicOr(err, kDevErrTimeout);
         }
       }
-      bool ok = !flag_read(&flags[0]) && mbar_wait_bounded(&full[s], static_cast<uint32_t>((it / S) & 1));
-      if (!ok && !flag_read(&flags[0])) {
-        flags[0] = 1;
-        atomicOr(err, kDevErrTimeout);
+      bool ok = false;
+      if (!dead) {
+        ok = __all_sync(0xffffffffu, mbar_wait_bounded(&full[s], ph));
+        if (!ok) {
+          dead = true;
+          if (lane == 0) {
+            flags[0] = 1;
+            atomicOr(err, kDevErrTimeout);
+          }
+        }
       }
       double hp = 0.0;
       if (active && ok) {
@@ -247,9 +257,16 @@ __global__ void __launch_bounds__(FDot<L>::kThreads) k_dot_frsz2(BasisView B, in
       }
       myred[(vec % C::kBatch) * C::kRedStride + lane] = hp;
       __syncwarp();
-      if (lane == 0) mbar_arrive(&empty[s]);
+      if (lane == 0 && ok) mbar_arrive(&empty[s]);
+      ps = s;
+      pph = ph;
+      first = false;
+      if (++s == S) {
+        s = 0;
+        ph ^= 1u;
+      }
       if (vec % C::kBatch == C::kBatch - 1 || vec == nvec - 1) {
-        const int first = vec - (vec % C::kBatch), cnt = vec - first + 1;
+        const int first_v = vec - (vec % C::kBatch), cnt = vec - first_v + 1;
         const int v = lane & 7, part = lane >> 3;
         double sacc = 0.0;
         if (v < cnt) {
@@ -258,12 +275,8 @@ __global__ void __launch_bounds__(FDot<L>::kThreads) k_dot_frsz2(BasisView B, in
         }
         sacc += __shfl_xor_sync(0xffffffffu, sacc, 8);
         sacc += __shfl_xor_sync(0xffffffffu, sacc, 16);
-        if (part == 0 && v < cnt) myh[first + v] += sacc;
+        if (part == 0 && v < cnt) myh[first_v + v] += sacc;
         __syncwarp();
-      }
-      if (flag_read(&flags[0])) {
-        aborted = true;
-        break;
       }
     }
   }
@@ -292,7 +305,7 @@ __global__ void __launch_bounds__(FDot<L>::kThreads) k_dot_frsz2(BasisView B, in
 }
 
 // ================================================================================================
-// update: 16 consecutive values per thread, 2 threads per block, 64 blocks per tile, vectors in
+// update: 8 consecutive values per thread, 4 threads per block, 32 blocks per tile, vectors in
 // groups of at most 32 (the exact integer sums are per group)
 // ================================================================================================
 
@@ -300,8 +313,8 @@ template <int L>
 struct FUpd {
   static constexpr int kThreads = 128;
   static constexpr int kWarps = 4;
-  static constexpr int kBlocks = 64;
-  static constexpr int kStages = 5;
+  static constexpr int kBlocks = 32;
+  static constexpr int kStages = 4;
   static constexpr int kGroup = 32;
   static constexpr int kStageBytes = kBlocks * L * 4;
   // dynamic smem: stages | coefficient table [kGroup][kBlocks] (int2) | exponent words of one group
@@ -318,54 +331,38 @@ struct HInfo {  // a coefficient h_i as sign, 53-bit integer significand and eff
   int neg;
 };
 
-// The 16 codes of this thread (values 16 h .. 16 h + 15 of block t/2, h = t%2) from a stage, in
-// register slots whose order is rotated by the thread index so that the threads of a shared-memory
-// phase hit distinct banks. slot_pos gives the value each slot holds.
+// The 8 codes of this thread (values 8 q .. 8 q + 7 of block t/4, q = t%4) from a stage. For l = 32
+// the two 16-byte chunks are read in an order swizzled by bit 2 of t so that the 8 threads of a
+// shared-memory phase hit distinct banks; slot k then holds value k ^ 4.
 template <int L>
-__device__ __forceinline__ void load_codes16(const uint32_t* st, int t, uint32_t (&c)[16]) {
+__device__ __forceinline__ void load_codes8(const uint32_t* st, int t, uint32_t (&c)[8]) {
   if (L == 32) {
-    const uint4* p = reinterpret_cast<const uint4*>(st) + 4 * t;
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      const uint4 a = p[(j + (t >> 1)) & 3];
-      c[4 * j] = a.x; c[4 * j + 1] = a.y; c[4 * j + 2] = a.z; c[4 * j + 3] = a.w;
-    }
+    const int swap = (t >> 2) & 1;
+    const uint4* p = reinterpret_cast<const uint4*>(st);
+    const uint4 a = p[2 * t + swap], b = p[2 * t + 1 - swap];
+    c[0] = a.x; c[1] = a.y; c[2] = a.z; c[3] = a.w;
+    c[4] = b.x; c[5] = b.y; c[6] = b.z; c[7] = b.w;
   } else if (L == 16) {
-    const uint4* p = reinterpret_cast<const uint4*>(st) + 2 * t;
-#pragma unroll
-    for (int j = 0; j < 2; ++j) {
-      const uint4 a = p[(j + (t >> 2)) & 1];
-      const uint32_t wv[4] = {a.x, a.y, a.z, a.w};
-#pragma unroll
-      for (int i = 0; i < 4; ++i) {
-        c[8 * j + 2 * i] = wv[i] & 0xFFFFu;
-        c[8 * j + 2 * i + 1] = wv[i] >> 16;
-      }
-    }
+    const uint4 a = reinterpret_cast<const uint4*>(st)[t];
+    c[0] = a.x & 0xFFFFu; c[1] = a.x >> 16; c[2] = a.y & 0xFFFFu; c[3] = a.y >> 16;
+    c[4] = a.z & 0xFFFFu; c[5] = a.z >> 16; c[6] = a.w & 0xFFFFu; c[7] = a.w >> 16;
   } else {
-    // codes 16 h .. 16 h + 15 of a block occupy stream bits [336 h, 336 h + 336)
-    const int blk = t >> 1, h = t & 1;
+    // the 8 codes of quarter q of a block occupy stream bits [168 q, 168 q + 168)
+    const int blk = t >> 2, q = t & 3;
     const uint32_t* bw = st + blk * 21;
-    const int wbase = h ? 10 : 0, o = h ? 16 : 0;
-    uint32_t raw[12];
+    const int wbase = (168 * q) >> 5, o = (168 * q) & 31;
+    uint32_t raw[7];
 #pragma unroll
-    for (int i = 0; i < 12; ++i) raw[i] = (wbase + i < 21) ? bw[wbase + i] : 0u;
-    uint32_t al[11];
+    for (int i = 0; i < 7; ++i) raw[i] = (wbase + i < 21) ? bw[wbase + i] : 0u;
+    uint32_t al[6];
 #pragma unroll
-    for (int i = 0; i < 11; ++i) al[i] = __funnelshift_r(raw[i], raw[i + 1], o);
+    for (int i = 0; i < 6; ++i) al[i] = __funnelshift_r(raw[i], raw[i + 1], o);
 #pragma unroll
-    for (int k = 0; k < 16; ++k) {
+    for (int k = 0; k < 8; ++k) {
       const int bit = 21 * k, a = bit >> 5, oo = bit & 31;
-      c[k] = __funnelshift_r(al[a], al[a + 1], oo) & 0x1FFFFFu;
+      c[k] = __funnelshift_r(al[a], a + 1 < 6 ? al[a + 1] : 0u, oo) & 0x1FFFFFu;
     }
   }
-}
-
-template <int L>
-__device__ __forceinline__ int slot_pos(int t, int k) {
-  if (L == 32) return 4 * (((k >> 2) + (t >> 1)) & 3) + (k & 3);
-  if (L == 16) return 8 * (((k >> 3) + (t >> 2)) & 1) + (k & 7);
-  return k;
 }
 
 template <int L>
@@ -392,7 +389,8 @@ __global__ void __launch_bounds__(FUpd<L>::kThreads) k_update_frsz2(BasisView B,
   int* flags = reinterpret_cast<int*>(ebar + 2);
 
   const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
-  const int blk = t >> 1, hq = t & 1;
+  const int blk = t >> 2, q = t & 3;
+  const bool sw = L == 32 && ((t >> 2) & 1);  // slot k holds value k ^ 4 (swizzled l = 32 loads)
   const int64_t nb = (B.n + 31) / 32;
   int64_t b0, b1;
   cta_block_range(nb, gridDim.x, blockIdx.x, &b0, &b1);
@@ -456,16 +454,22 @@ __global__ void __launch_bounds__(FUpd<L>::kThreads) k_update_frsz2(BasisView B,
   int egroups = 0;  // exponent copies consumed so far (phase of ebar)
 
   double nrm = 0.0;
-  int it = 0;
+  int s = 0;            // stage of the current vector
+  uint32_t ph = 0;      // phase parity of that stage's barriers
+  int ps = 0;           // stage and phase parity of the previous vector (refilled next)
+  uint32_t pph = 0;
+  bool first = true;
+  bool dead = false;    // this warp gave up waiting (warp-uniform; it then only runs to the next barrier)
+  bool rfail = false;   // thread 0 gave up waiting for a stage to be released (no more refills)
   bool aborted = false;
   for (int tile = 0; tile < ntiles && !aborted; ++tile) {
     const int64_t tb0 = b0 + (int64_t)tile * NBT;
     const int nbt = static_cast<int>(min((int64_t)NBT, b1 - tb0));
     const bool active = blk < nbt;
-    const int64_t k0 = (tb0 + blk) * 32 + hq * 16;  // first of this thread's 16 values
-    double dacc[16];
+    const int64_t k0 = (tb0 + blk) * 32 + q * 8;  // first of this thread's 8 values
+    double dacc[8];
 #pragma unroll
-    for (int k = 0; k < 16; ++k) dacc[k] = 0.0;
+    for (int k = 0; k < 8; ++k) dacc[k] = 0.0;
     for (int g0 = 0; g0 < nvec; g0 += G) {
       const int gn = min(G, nvec - g0);
       __syncthreads();  // the previous group's coefficient table is no longer read
@@ -480,22 +484,23 @@ __global__ void __launch_bounds__(FUpd<L>::kThreads) k_update_frsz2(BasisView B,
         atomicOr(err, kDevErrTimeout);
       }
       // rexp = max over the group of (Eh_i + Ebar_{i,b}): exponent of the block's largest term;
-      // the 2 threads of a block split the group's vectors and combine with a shuffle.
-      uint32_t ev[G / 2];
+      // the 4 threads of a block split the group's vectors and combine with shuffles.
+      uint32_t ev[G / 4];
       int r = 0;
 #pragma unroll
-      for (int kk = 0; kk < G / 2; ++kk) {
-        const int v = hq + 2 * kk;
+      for (int kk = 0; kk < G / 4; ++kk) {
+        const int v = q + 4 * kk;
         const uint32_t e = (v < gn && active && eok) ? exq[v * NBT + blk] : 0u;
         ev[kk] = e;
         if (v < gn) r = max(r, hinfo[g0 + v].eff + (e > 1 ? static_cast<int>(e) : 1));
       }
       r = max(r, __shfl_xor_sync(0xffffffffu, r, 1));
+      r = max(r, __shfl_xor_sync(0xffffffffu, r, 2));
       // G_{i,b} = round(Mh_i 2^{Eh_i + Ebar_{i,b} - rexp}) with sign, |G| < 2^53, as
       // G0 = G mod 2^27 in [0, 2^27) and G1 = floor(G / 2^27) in [-2^26, 2^26)
 #pragma unroll
-      for (int kk = 0; kk < G / 2; ++kk) {
-        const int v = hq + 2 * kk;
+      for (int kk = 0; kk < G / 4; ++kk) {
+        const int v = q + 4 * kk;
         if (v < gn) {
           const HInfo hi = hinfo[g0 + v];
           const uint32_t e = ev[kk];
@@ -504,7 +509,6 @@ __global__ void __launch_bounds__(FUpd<L>::kThreads) k_update_frsz2(BasisView B,
           if (sh == 0) mag = hi.mant;
           else if (sh < 64) mag = ((hi.mant >> (sh - 1)) + 1) >> 1;
           else mag = 0;
-          if (mag >> 53) mag = (1ull << 53) - 1;  // rounding up to 2^53: stay below it
           const int64_t gm = hi.neg ? -static_cast<int64_t>(mag) : static_cast<int64_t>(mag);
           gam[v * NBT + blk] = make_int2(static_cast<int32_t>(gm & ((1ll << 27) - 1)), static_cast<int32_t>(gm >> 27));
         }
@@ -520,34 +524,38 @@ __global__ void __launch_bounds__(FUpd<L>::kThreads) k_update_frsz2(BasisView B,
           ++eissued;
         }
       }
-      long long acc0[16], acc1[16];
+      long long acc0[8], acc1[8];
 #pragma unroll
-      for (int k = 0; k < 16; ++k) acc0[k] = acc1[k] = 0;
-      for (int v = 0; v < gn; ++v, ++it) {
-        // After an abort the loop keeps running without waiting or computing, so that every thread
-        // reaches the next CTA barrier.
-        const int s = it % S;
-        if (t == 0 && it >= 1 && issued < total && !flag_read(&flags[0])) {
-          const int sp = (it - 1) % S;
-          if (mbar_wait_bounded(&empty[sp], static_cast<uint32_t>(((it - 1) / S) & 1))) {
+      for (int k = 0; k < 8; ++k) acc0[k] = acc1[k] = 0;
+      for (int v = 0; v < gn; ++v) {
+        // lagged refill (thread 0): the stage every warp released in the previous iteration
+        if (t == 0 && !first && issued < total && !rfail && !dead) {
+          if (mbar_wait_bounded(&empty[ps], pph)) {
             issue(issued);
             ++issued;
           } else {
+            rfail = true;
             flags[0] = 1;
             atomicOr(err, kDevErrTimeout);
           }
         }
-        bool ok = !flag_read(&flags[0]) && mbar_wait_bounded(&full[s], static_cast<uint32_t>((it / S) & 1));
-        if (!ok && !flag_read(&flags[0])) {
-          flags[0] = 1;
-          atomicOr(err, kDevErrTimeout);
+        bool ok = false;
+        if (!dead) {
+          ok = __all_sync(0xffffffffu, mbar_wait_bounded(&full[s], ph));
+          if (!ok) {
+            dead = true;
+            if (lane == 0) {
+              flags[0] = 1;
+              atomicOr(err, kDevErrTimeout);
+            }
+          }
         }
         if (active && ok) {
-          uint32_t c[16];
-          load_codes16<L>(reinterpret_cast<const uint32_t*>(stages + s * C::kStageBytes), t, c);
+          uint32_t c[8];
+          load_codes8<L>(reinterpret_cast<const uint32_t*>(stages + s * C::kStageBytes), t, c);
           const int2 gp = gam[v * NBT + blk];
 #pragma unroll
-          for (int k = 0; k < 16; ++k) {
+          for (int k = 0; k < 8; ++k) {
             const int32_t sv = code_to_int<L>(c[k]);
             mac_wide(acc0[k], sv, gp.x);
             mac_wide(acc1[k], sv, gp.y);
@@ -555,42 +563,49 @@ __global__ void __launch_bounds__(FUpd<L>::kThreads) k_update_frsz2(BasisView B,
         }
         __syncwarp();
         if (lane == 0 && ok) mbar_arrive(&empty[s]);
+        ps = s;
+        pph = ph;
+        first = false;
+        if (++s == S) {
+          s = 0;
+          ph ^= 1u;
+        }
       }
-      if (active && !flag_read(&flags[0])) {
+      if (active && !dead) {
         // sum_i s G = acc1 2^27 + acc0 exactly (|.| < 2^(l+57)), scale 2^{rexp - 2096 - l}; rounded
         // to 2^(l-5) units (at most 2^-58 of the block's largest possible term, 2^(l+52) units) and
         // converted once per value
         const int x = r - 2096 - 5;
 #pragma unroll
-        for (int k = 0; k < 16; ++k) {
+        for (int k = 0; k < 8; ++k) {
           const long long th = (acc1[k] << (32 - L)) + ((acc0[k] + (1ll << (L - 6))) >> (L - 5));
           dacc[k] += scale_pow2(static_cast<double>(th), x);
         }
       }
     }
-    if (aborted || flag_read(&flags[0])) break;
+    if (aborted || dead) continue;
     if (active) {
-      if (k0 + 16 <= B.n) {
-        // values in slot order: chunks of 4 (l = 32), 8 (l = 16) or 16 (l = 21) consecutive values
-        constexpr int CH = (L == 32) ? 4 : (L == 16 ? 8 : 16);
+      if (k0 + 8 <= B.n) {
+        double2* p = reinterpret_cast<double2*>(w + k0);
+        double cur[8];
 #pragma unroll
-        for (int j = 0; j < 16 / CH; ++j) {
-          const int pos = slot_pos<L>(t, j * CH);
-          double2* p = reinterpret_cast<double2*>(w + k0 + pos);
+        for (int i = 0; i < 4; ++i) {
+          const double2 v = p[i];
+          cur[2 * i] = v.x;
+          cur[2 * i + 1] = v.y;
+        }
 #pragma unroll
-          for (int i = 0; i < CH / 2; ++i) {
-            double2 v = p[i];
-            v.x -= dacc[j * CH + 2 * i];
-            v.y -= dacc[j * CH + 2 * i + 1];
-            p[i] = v;
-            nrm = fma(v.x, v.x, nrm);
-            nrm = fma(v.y, v.y, nrm);
-          }
+        for (int k = 0; k < 8; ++k) cur[k] -= sw ? dacc[k ^ 4] : dacc[k];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          p[i] = make_double2(cur[2 * i], cur[2 * i + 1]);
+          nrm = fma(cur[2 * i], cur[2 * i], nrm);
+          nrm = fma(cur[2 * i + 1], cur[2 * i + 1], nrm);
         }
       } else {
 #pragma unroll
-        for (int k = 0; k < 16; ++k) {
-          const int64_t idx = k0 + slot_pos<L>(t, k);
+        for (int k = 0; k < 8; ++k) {
+          const int64_t idx = k0 + (sw ? (k ^ 4) : k);
           if (idx < B.n) {
             const double nv = w[idx] - dacc[k];
             w[idx] = nv;
@@ -605,8 +620,8 @@ __global__ void __launch_bounds__(FUpd<L>::kThreads) k_update_frsz2(BasisView B,
     if (t == 0) {
       for (int p = max(0, issued - S); p < issued; ++p)
         mbar_wait_bounded(&full[p % S], static_cast<uint32_t>((p / S) & 1));
+      if (eissued > egroups) mbar_wait_bounded(&ebar[0], static_cast<uint32_t>(egroups & 1));
     }
-    if (warp == 0 && lane == 0 && eissued > egroups) mbar_wait_bounded(&ebar[0], static_cast<uint32_t>(egroups & 1));
     return;
   }
   // ||w||^2: CTA partial, then the last CTA reduces all partials in a fixed order
