@@ -11,9 +11,10 @@
 //           (at most l+57 bits) is rounded to 2^(l-5) units in integer arithmetic and converted
 //           once per (vector, block), then summed in FP64 (per warp, per CTA, across CTAs in a
 //           fixed order).
-//   update  sum_i s_{i,k} G_{i,b}, G the 54-bit fixed point of h_i 2^{q_{i,b}} against the
-//           block's largest term over a group of at most 32 vectors, is exact in two 64-bit
-//           accumulators (27-bit pieces of G) and converted once per element and group.
+//   update  sum_i s_{i,k} G_{i,b}, G = rint(h_i 2^{q_{i,b}}) at a per-block fixed point that puts
+//           the block's largest term at 53 bits (one exact FP64 scaling and one rounding per
+//           (vector, block)), is exact in two 64-bit accumulators (27-bit pieces of G) over a group
+//           of at most 32 vectors, and converted once per element and group.
 //
 // The basis is streamed with 1D bulk copies (TMA) into a ring of shared-memory stages. Each stage
 // has a "full" mbarrier (the copy's transaction count) and an "empty" mbarrier (one arrival per
@@ -305,8 +306,8 @@ __global__ void __launch_bounds__(FDot<L>::kThreads) k_dot_frsz2(BasisView B, in
 }
 
 // ================================================================================================
-// update: 8 consecutive values per thread, 4 threads per block, 32 blocks per tile, vectors in
-// groups of at most 32 (the exact integer sums are per group)
+// update: 8 consecutive values per thread, 4 threads per block, 32 blocks per tile, two basis vectors
+// per pipeline stage, vectors in groups of at most 32 (the exact integer sums are per group)
 // ================================================================================================
 
 template <int L>
@@ -314,26 +315,22 @@ struct FUpd {
   static constexpr int kThreads = 128;
   static constexpr int kWarps = 4;
   static constexpr int kBlocks = 32;
-  static constexpr int kStages = 4;
+  static constexpr int kVps = 2;  // basis vectors per stage
+  static constexpr int kStages = 3;
   static constexpr int kGroup = 32;
-  static constexpr int kStageBytes = kBlocks * L * 4;
+  static constexpr int kVecBytes = kBlocks * L * 4;
+  static constexpr int kStageBytes = kVps * kVecBytes;
   // dynamic smem: stages | coefficient table [kGroup][kBlocks] (int2) | exponent words of one group
-  //               [kGroup][kBlocks] | hinfo[nvec_max] | red[kWarps] | full, empty, exps barriers | flags
+  //               [kGroup][kBlocks] | h[nvec_max] | red[kWarps] | full, empty, exps barriers | flags
   static size_t smem_bytes(int nvec_max) {
     return (size_t)kStages * kStageBytes + (size_t)kGroup * kBlocks * 8 + (size_t)kGroup * kBlocks * 4 +
-           (size_t)nvec_max * 16 + kWarps * 8 + (2 * kStages + 2) * 8 + 16;
+           (size_t)(nvec_max + 1) * 8 + kWarps * 8 + (2 * kStages + 2) * 8 + 16;
   }
 };
 
-struct HInfo {  // a coefficient h_i as sign, 53-bit integer significand and effective exponent
-  unsigned long long mant;
-  int eff;
-  int neg;
-};
-
-// The 8 codes of this thread (values 8 q .. 8 q + 7 of block t/4, q = t%4) from a stage. For l = 32
-// the two 16-byte chunks are read in an order swizzled by bit 2 of t so that the 8 threads of a
-// shared-memory phase hit distinct banks; slot k then holds value k ^ 4.
+// The 8 codes of this thread (values 8 q .. 8 q + 7 of block t/4, q = t%4) of one vector in a stage.
+// For l = 32 the two 16-byte chunks are read in an order swizzled by bit 2 of t so that the 8 threads
+// of a shared-memory phase hit distinct banks; slot k then holds value k ^ 4.
 template <int L>
 __device__ __forceinline__ void load_codes8(const uint32_t* st, int t, uint32_t (&c)[8]) {
   if (L == 32) {
@@ -373,7 +370,7 @@ __global__ void __launch_bounds__(FUpd<L>::kThreads) k_update_frsz2(BasisView B,
                                                                     unsigned int* counter, int* err, NormEpilogue epi,
                                                                     Gate gate) {
   using C = FUpd<L>;
-  constexpr int T = C::kThreads, NBT = C::kBlocks, G = C::kGroup, S = C::kStages;
+  constexpr int T = C::kThreads, NBT = C::kBlocks, G = C::kGroup, S = C::kStages, VPS = C::kVps;
   if (gate_skip(gate)) return;
   const int nvec = nvec_dev ? *(volatile const int*)nvec_dev : nvec_arg;
   const int nvec_cap = nvec_dev ? nvec_arg : nvec;
@@ -381,8 +378,8 @@ __global__ void __launch_bounds__(FUpd<L>::kThreads) k_update_frsz2(BasisView B,
   uint8_t* stages = smem;
   int2* gam = reinterpret_cast<int2*>(smem + S * C::kStageBytes);
   uint32_t* exq = reinterpret_cast<uint32_t*>(gam + G * NBT);
-  HInfo* hinfo = reinterpret_cast<HInfo*>(exq + G * NBT);
-  double* red = reinterpret_cast<double*>(hinfo + nvec_cap);
+  double* hval = reinterpret_cast<double*>(exq + G * NBT);
+  double* red = hval + nvec_cap + 1;
   uint64_t* full = reinterpret_cast<uint64_t*>(red + C::kWarps);
   uint64_t* empty = full + S;
   uint64_t* ebar = empty + S;  // exponent words of the next group ([1] unused, keeps alignment)
@@ -395,18 +392,10 @@ __global__ void __launch_bounds__(FUpd<L>::kThreads) k_update_frsz2(BasisView B,
   int64_t b0, b1;
   cta_block_range(nb, gridDim.x, blockIdx.x, &b0, &b1);
   const int ntiles = static_cast<int>((b1 - b0 + NBT - 1) / NBT);
-  const int total = ntiles * nvec;
+  const int units = (nvec + VPS - 1) / VPS;  // stages per tile
+  const int total = ntiles * units;
 
-  for (int i = t; i < nvec; i += T) {
-    const double h = negate ? -hcoef[i] : hcoef[i];
-    const uint64_t u = static_cast<uint64_t>(__double_as_longlong(h));
-    const int e = static_cast<int>((u >> 52) & 0x7FF);
-    HInfo hi;
-    hi.mant = (u & ((1ull << 52) - 1)) | (e ? (1ull << 52) : 0ull);
-    hi.eff = e > 1 ? e : 1;
-    hi.neg = static_cast<int>(u >> 63);
-    hinfo[i] = hi;
-  }
+  for (int i = t; i < nvec; i += T) hval[i] = negate ? -hcoef[i] : hcoef[i];
   if (t == 0) {
     for (int s = 0; s < S; ++s) {
       mbar_init(&full[s], 1);
@@ -418,14 +407,17 @@ __global__ void __launch_bounds__(FUpd<L>::kThreads) k_update_frsz2(BasisView B,
   }
   __syncthreads();
 
-  auto issue = [&](int p) {
-    const int tile = p / nvec, vec = p - tile * nvec, s = p % S;
+  auto issue = [&](int p) {  // stage unit p: vectors VPS u .. of tile p / units
+    const int tile = p / units, u = p - tile * units, s = p % S;
+    const int v0 = u * VPS, nv = min(VPS, nvec - v0);
     const int64_t tb0 = b0 + (int64_t)tile * NBT;
     const int nbt = static_cast<int>(min((int64_t)NBT, b1 - tb0));
     const uint32_t cbytes = static_cast<uint32_t>((nbt * L * 4 + 15) & ~15);
     fence_proxy_async_smem();
-    mbar_arrive_expect_tx(&full[s], cbytes);
-    bulk_g2s(stages + s * C::kStageBytes, B.vals + (int64_t)vec * B.vstride + tb0 * L * 4, cbytes, &full[s]);
+    mbar_arrive_expect_tx(&full[s], cbytes * nv);
+    for (int j = 0; j < nv; ++j)
+      bulk_g2s(stages + s * C::kStageBytes + j * C::kVecBytes, B.vals + (int64_t)(v0 + j) * B.vstride + tb0 * L * 4,
+               cbytes, &full[s]);
   };
   // Exponent words of group [g0, g0 + G) for tile `tile`, one bulk copy per vector into exq[v][*],
   // issued by the 32 lanes of warp 0 (lane 0 first posts the expected byte count).
@@ -454,9 +446,9 @@ __global__ void __launch_bounds__(FUpd<L>::kThreads) k_update_frsz2(BasisView B,
   int egroups = 0;  // exponent copies consumed so far (phase of ebar)
 
   double nrm = 0.0;
-  int s = 0;            // stage of the current vector
-  uint32_t ph = 0;      // phase parity of that stage's barriers
-  int ps = 0;           // stage and phase parity of the previous vector (refilled next)
+  int s = 0;            // stage of the current unit and the phase parity of its barriers
+  uint32_t ph = 0;
+  int ps = 0;           // stage and parity of the previous unit (refilled by thread 0)
   uint32_t pph = 0;
   bool first = true;
   bool dead = false;    // this warp gave up waiting (warp-uniform; it then only runs to the next barrier)
@@ -492,24 +484,18 @@ __global__ void __launch_bounds__(FUpd<L>::kThreads) k_update_frsz2(BasisView B,
         const int v = q + 4 * kk;
         const uint32_t e = (v < gn && active && eok) ? exq[v * NBT + blk] : 0u;
         ev[kk] = e;
-        if (v < gn) r = max(r, hinfo[g0 + v].eff + (e > 1 ? static_cast<int>(e) : 1));
+        if (v < gn) r = max(r, eff_exp(hval[g0 + v]) + (e > 1 ? static_cast<int>(e) : 1));
       }
       r = max(r, __shfl_xor_sync(0xffffffffu, r, 1));
       r = max(r, __shfl_xor_sync(0xffffffffu, r, 2));
-      // G_{i,b} = round(Mh_i 2^{Eh_i + Ebar_{i,b} - rexp}) with sign, |G| < 2^53, as
-      // G0 = G mod 2^27 in [0, 2^27) and G1 = floor(G / 2^27) in [-2^26, 2^26)
+      // G_{i,b} = rint(h_i 2^{Ebar_{i,b} + 1075 - rexp}): the exact power-of-two scaling puts the
+      // block's largest term at 53 bits, |G| < 2^53; stored as G0 = G mod 2^27, G1 = floor(G / 2^27)
 #pragma unroll
       for (int kk = 0; kk < G / 4; ++kk) {
         const int v = q + 4 * kk;
         if (v < gn) {
-          const HInfo hi = hinfo[g0 + v];
           const uint32_t e = ev[kk];
-          const int sh = r - (hi.eff + (e > 1 ? static_cast<int>(e) : 1));
-          uint64_t mag;
-          if (sh == 0) mag = hi.mant;
-          else if (sh < 64) mag = ((hi.mant >> (sh - 1)) + 1) >> 1;
-          else mag = 0;
-          const int64_t gm = hi.neg ? -static_cast<int64_t>(mag) : static_cast<int64_t>(mag);
+          const long long gm = __double2ll_rn(scale_pow2(hval[g0 + v], (e > 1 ? static_cast<int>(e) : 1) + 1075 - r));
           gam[v * NBT + blk] = make_int2(static_cast<int32_t>(gm & ((1ll << 27) - 1)), static_cast<int32_t>(gm >> 27));
         }
       }
@@ -527,7 +513,7 @@ __global__ void __launch_bounds__(FUpd<L>::kThreads) k_update_frsz2(BasisView B,
       long long acc0[8], acc1[8];
 #pragma unroll
       for (int k = 0; k < 8; ++k) acc0[k] = acc1[k] = 0;
-      for (int v = 0; v < gn; ++v) {
+      for (int v = 0; v < gn; v += VPS) {
         // lagged refill (thread 0): the stage every warp released in the previous iteration
         if (t == 0 && !first && issued < total && !rfail && !dead) {
           if (mbar_wait_bounded(&empty[ps], pph)) {
@@ -551,14 +537,20 @@ __global__ void __launch_bounds__(FUpd<L>::kThreads) k_update_frsz2(BasisView B,
           }
         }
         if (active && ok) {
-          uint32_t c[8];
-          load_codes8<L>(reinterpret_cast<const uint32_t*>(stages + s * C::kStageBytes), t, c);
-          const int2 gp = gam[v * NBT + blk];
+          const uint8_t* st = stages + s * C::kStageBytes;
 #pragma unroll
-          for (int k = 0; k < 8; ++k) {
-            const int32_t sv = code_to_int<L>(c[k]);
-            mac_wide(acc0[k], sv, gp.x);
-            mac_wide(acc1[k], sv, gp.y);
+          for (int j = 0; j < VPS; ++j) {
+            if (j == 0 || v + 1 < gn) {
+              uint32_t c[8];
+              load_codes8<L>(reinterpret_cast<const uint32_t*>(st + j * C::kVecBytes), t, c);
+              const int2 gp = gam[(v + j) * NBT + blk];
+#pragma unroll
+              for (int k = 0; k < 8; ++k) {
+                const int32_t sv = code_to_int<L>(c[k]);
+                mac_wide(acc0[k], sv, gp.x);
+                mac_wide(acc1[k], sv, gp.y);
+              }
+            }
           }
         }
         __syncwarp();
