@@ -36,6 +36,13 @@ __device__ __forceinline__ void mac_wide(long long& acc, int32_t a, int32_t b) {
   acc += p;
 }
 
+// x / 2^d rounded to nearest (ties up) for |x| < 2^62 and d >= 0.
+__device__ __forceinline__ long long round_shift_right(long long x, int d) {
+  if (d <= 0) return x;
+  if (d > 62) return 0;
+  return (x + (1ll << (d - 1))) >> d;
+}
+
 // Prefetch `bytes` (multiple of 16, 16-byte aligned) of global memory into L2 with the bulk-copy unit.
 __device__ __forceinline__ void bulk_prefetch_l2(const void* p, uint32_t bytes) {
   asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");

@@ -11,10 +11,11 @@
 //           (at most l+57 bits) is rounded to 2^(l-5) units in integer arithmetic and converted
 //           once per (vector, block), then summed in FP64 (per warp, per CTA, across CTAs in a
 //           fixed order).
-//   update  sum_i s_{i,k} G_{i,b}, G = rint(h_i 2^{q_{i,b}}) at a per-block fixed point that puts
-//           the block's largest term at 53 bits (one exact FP64 scaling and one rounding per
-//           (vector, block)), is exact in two 64-bit accumulators (27-bit pieces of G) over a group
-//           of at most 32 vectors, and converted once per element and group.
+//   update  sum_i s_{i,k} G_{i,b}, G the 54-bit fixed point of h_i 2^{q_{i,b}} against the block's
+//           largest term within a group of at most 32 vectors (an integer mantissa shift per
+//           (vector, block)), is exact in two 64-bit accumulators (27-bit pieces of G). Groups are
+//           combined in a 64-bit integer per element at the larger of their block scales, and the
+//           element is converted to FP64 once: FP64 work is per element, not per element and group.
 //
 // The basis is streamed with 1D bulk copies (TMA) into a ring of shared-memory stages. Each stage
 // has a "full" mbarrier (the copy's transaction count) and an "empty" mbarrier (one arrival per
@@ -318,13 +319,18 @@ struct FUpd {
   static constexpr int kVps = 2;  // basis vectors per stage
   static constexpr int kStages = 3;
   static constexpr int kGroup = 32;
+  // resident CTAs per SM the register allocation is capped for (l < 32 is faster with a few spills
+  // and one more CTA)
+  static constexpr int kMinBlocks = L == 32 ? 5 : 6;
   static constexpr int kVecBytes = kBlocks * L * 4;
   static constexpr int kStageBytes = kVps * kVecBytes;
   // dynamic smem: stages | coefficient table [kGroup][kBlocks] (int2) | exponent words of one group
-  //               [kGroup][kBlocks] | h[nvec_max] | red[kWarps] | full, empty, exps barriers | flags
+  //               [kGroup][kBlocks] | mantissas of h [nvec_max + 1] (int64) | exponents of h
+  //               [nvec_max + 2] (int) | red[kWarps] | full, empty, exps barriers | flags
   static size_t smem_bytes(int nvec_max) {
     return (size_t)kStages * kStageBytes + (size_t)kGroup * kBlocks * 8 + (size_t)kGroup * kBlocks * 4 +
-           (size_t)(nvec_max + 1) * 8 + kWarps * 8 + (2 * kStages + 2) * 8 + 16;
+           (size_t)(nvec_max + 1) * 8 + (size_t)((nvec_max + 2) & ~1) * 4 + kWarps * 8 + (2 * kStages + 2) * 8 +
+           16;
   }
 };
 
@@ -363,7 +369,7 @@ __device__ __forceinline__ void load_codes8(const uint32_t* st, int t, uint32_t 
 }
 
 template <int L>
-__global__ void __launch_bounds__(FUpd<L>::kThreads) k_update_frsz2(BasisView B, int nvec_arg, const int* nvec_dev,
+__global__ void __launch_bounds__(FUpd<L>::kThreads, FUpd<L>::kMinBlocks) k_update_frsz2(BasisView B, int nvec_arg, const int* nvec_dev,
                                                                     const double* __restrict__ hcoef, int negate,
                                                                     double* __restrict__ w,
                                                                     double* __restrict__ partials,
@@ -378,8 +384,9 @@ __global__ void __launch_bounds__(FUpd<L>::kThreads) k_update_frsz2(BasisView B,
   uint8_t* stages = smem;
   int2* gam = reinterpret_cast<int2*>(smem + S * C::kStageBytes);
   uint32_t* exq = reinterpret_cast<uint32_t*>(gam + G * NBT);
-  double* hval = reinterpret_cast<double*>(exq + G * NBT);
-  double* red = hval + nvec_cap + 1;
+  long long* hman = reinterpret_cast<long long*>(exq + G * NBT);  // signed 53-bit mantissa of h_i
+  int* hexp = reinterpret_cast<int*>(hman + nvec_cap + 1);        // its effective IEEE exponent
+  double* red = reinterpret_cast<double*>(hexp + ((nvec_cap + 2) & ~1));
   uint64_t* full = reinterpret_cast<uint64_t*>(red + C::kWarps);
   uint64_t* empty = full + S;
   uint64_t* ebar = empty + S;  // exponent words of the next group ([1] unused, keeps alignment)
@@ -395,7 +402,19 @@ __global__ void __launch_bounds__(FUpd<L>::kThreads) k_update_frsz2(BasisView B,
   const int units = (nvec + VPS - 1) / VPS;  // stages per tile
   const int total = ntiles * units;
 
-  for (int i = t; i < nvec; i += T) hval[i] = negate ? -hcoef[i] : hcoef[i];
+  // h_i = hman_i 2^{hexp_i - 1075} exactly (subnormals: hexp 1, no implicit bit)
+  for (int i = t; i < nvec; i += T) {
+    const uint64_t u = static_cast<uint64_t>(__double_as_longlong(hcoef[i]));
+    const int e = static_cast<int>((u >> 52) & 0x7FF);
+    const long long m = static_cast<long long>((u & ((1ull << 52) - 1)) | (e ? 1ull << 52 : 0ull));
+    hman[i] = ((u >> 63) != 0) != (negate != 0) ? -m : m;
+    hexp[i] = e > 1 ? e : 1;
+  }
+  // The group sums are kept in units of 2^(sh) against their block scale, sh = l - 5 + gb, so
+  // that up to 2^gb of them add up in 63 bits.
+  const int ngroups = (nvec + G - 1) / G;
+  const int gb = ngroups > 1 ? 32 - __clz(ngroups - 1) : 0;
+  const int sh = L - 5 + gb;
   if (t == 0) {
     for (int s = 0; s < S; ++s) {
       mbar_init(&full[s], 1);
@@ -459,9 +478,11 @@ __global__ void __launch_bounds__(FUpd<L>::kThreads) k_update_frsz2(BasisView B,
     const int nbt = static_cast<int>(min((int64_t)NBT, b1 - tb0));
     const bool active = blk < nbt;
     const int64_t k0 = (tb0 + blk) * 32 + q * 8;  // first of this thread's 8 values
-    double dacc[8];
+    // sum over the groups so far, in units of 2^(rc - 2101 + gb)
+    long long tacc[8];
 #pragma unroll
-    for (int k = 0; k < 8; ++k) dacc[k] = 0.0;
+    for (int k = 0; k < 8; ++k) tacc[k] = 0;
+    int rc = 0;
     for (int g0 = 0; g0 < nvec; g0 += G) {
       const int gn = min(G, nvec - g0);
       __syncthreads();  // the previous group's coefficient table is no longer read
@@ -484,18 +505,21 @@ __global__ void __launch_bounds__(FUpd<L>::kThreads) k_update_frsz2(BasisView B,
         const int v = q + 4 * kk;
         const uint32_t e = (v < gn && active && eok) ? exq[v * NBT + blk] : 0u;
         ev[kk] = e;
-        if (v < gn) r = max(r, eff_exp(hval[g0 + v]) + (e > 1 ? static_cast<int>(e) : 1));
+        if (v < gn) r = max(r, hexp[g0 + v] + (e > 1 ? static_cast<int>(e) : 1));
       }
       r = max(r, __shfl_xor_sync(0xffffffffu, r, 1));
       r = max(r, __shfl_xor_sync(0xffffffffu, r, 2));
-      // G_{i,b} = rint(h_i 2^{Ebar_{i,b} + 1075 - rexp}): the exact power-of-two scaling puts the
-      // block's largest term at 53 bits, |G| < 2^53; stored as G0 = G mod 2^27, G1 = floor(G / 2^27)
+      // G_{i,b} = h_i 2^{Ebar_{i,b} + 1075 - rexp} rounded to an integer (half up): the mantissa of
+      // h_i shifted right by rexp - hexp_i - Ebar_{i,b} >= 0, which puts the block's largest term at
+      // 53 bits, |G| <= 2^53; stored as G0 = G mod 2^27, G1 = floor(G / 2^27)
 #pragma unroll
       for (int kk = 0; kk < G / 4; ++kk) {
         const int v = q + 4 * kk;
         if (v < gn) {
           const uint32_t e = ev[kk];
-          const long long gm = __double2ll_rn(scale_pow2(hval[g0 + v], (e > 1 ? static_cast<int>(e) : 1) + 1075 - r));
+          const int d = r - hexp[g0 + v] - (e > 1 ? static_cast<int>(e) : 1);
+          const long long m = hman[g0 + v];
+          const long long gm = d == 0 ? m : (d < 64 ? ((m >> (d - 1)) + 1) >> 1 : 0);
           gam[v * NBT + blk] = make_int2(static_cast<int32_t>(gm & ((1ll << 27) - 1)), static_cast<int32_t>(gm >> 27));
         }
       }
@@ -564,18 +588,43 @@ __global__ void __launch_bounds__(FUpd<L>::kThreads) k_update_frsz2(BasisView B,
         }
       }
       if (active && !dead) {
-        // sum_i s G = acc1 2^27 + acc0 exactly (|.| < 2^(l+57)), scale 2^{rexp - 2096 - l}; rounded
-        // to 2^(l-5) units (at most 2^-58 of the block's largest possible term, 2^(l+52) units) and
-        // converted once per value
-        const int x = r - 2096 - 5;
+        // sum_i s G = acc1 2^27 + acc0 exactly (|.| < 2^(l+57)) at scale 2^{rexp - 2096 - l}, rounded
+        // to units of 2^sh (at most 2^(gb-58) of the block's largest possible term, 2^(l+52) units):
+        // |th| < 2^(62-gb). It joins the running sum at the larger of the two block scales; every
+        // rescaling rounds to nearest, again at most 2^(gb-58) of the larger largest term.
+        long long th[8];
+        if (sh <= 27) {
 #pragma unroll
-        for (int k = 0; k < 8; ++k) {
-          const long long th = (acc1[k] << (32 - L)) + ((acc0[k] + (1ll << (L - 6))) >> (L - 5));
-          dacc[k] += scale_pow2(static_cast<double>(th), x);
+          for (int k = 0; k < 8; ++k) th[k] = (acc1[k] << (27 - sh)) + ((acc0[k] + (1ll << (sh - 1))) >> sh);
+        } else {
+#pragma unroll
+          for (int k = 0; k < 8; ++k) {
+            const long long x = acc1[k] + (acc0[k] >> 27);
+            const long long y = (acc0[k] & ((1ll << 27) - 1)) + (1ll << (sh - 1));
+            th[k] = (x + (y >> 27)) >> (sh - 27);
+          }
+        }
+        if (g0 == 0 || r >= rc) {
+          const int dd = g0 == 0 ? 0 : r - rc;
+#pragma unroll
+          for (int k = 0; k < 8; ++k) tacc[k] = round_shift_right(tacc[k], dd) + th[k];
+          rc = r;
+        } else {
+#pragma unroll
+          for (int k = 0; k < 8; ++k) tacc[k] += round_shift_right(th[k], rc - r);
         }
       }
     }
     if (aborted || dead) continue;
+    // value k: w_k - tacc_k 2^x, one conversion and one fused multiply-add (the product tv 2^x is
+    // exact in the normal range, so the FMA rounds exactly like the subtraction of the product)
+    double tv[8];
+    const int x = rc - 2101 + gb;
+    const bool xnorm = x >= -1022 && x <= 1023;
+    const double p2 = -pow2_normal(xnorm ? x : 0);
+#pragma unroll
+    for (int k = 0; k < 8; ++k) tv[k] = static_cast<double>(tacc[k]);
+    auto sub = [&](double wk, double t) { return xnorm ? fma(t, p2, wk) : wk - scale_pow2(t, x); };
     if (active) {
       if (k0 + 8 <= B.n) {
         double2* p = reinterpret_cast<double2*>(w + k0);
@@ -587,7 +636,7 @@ __global__ void __launch_bounds__(FUpd<L>::kThreads) k_update_frsz2(BasisView B,
           cur[2 * i + 1] = v.y;
         }
 #pragma unroll
-        for (int k = 0; k < 8; ++k) cur[k] -= sw ? dacc[k ^ 4] : dacc[k];
+        for (int k = 0; k < 8; ++k) cur[k] = sub(cur[k], sw ? tv[k ^ 4] : tv[k]);
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
           p[i] = make_double2(cur[2 * i], cur[2 * i + 1]);
@@ -599,7 +648,7 @@ __global__ void __launch_bounds__(FUpd<L>::kThreads) k_update_frsz2(BasisView B,
         for (int k = 0; k < 8; ++k) {
           const int64_t idx = k0 + (sw ? (k ^ 4) : k);
           if (idx < B.n) {
-            const double nv = w[idx] - dacc[k];
+            const double nv = sub(w[idx], tv[k]);
             w[idx] = nv;
             nrm = fma(nv, nv, nrm);
           }

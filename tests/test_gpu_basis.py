@@ -8,7 +8,9 @@ so the comparison measures the GPU's own error. The tolerance follows from the G
 FRSZ2 blocks are summed exactly against a round-to-nearest 54-bit block fixed point of w (error at
 most 2^-54 max_{k in b}|w_k| per unit of |vhat|), cross-block and cross-CTA sums are FP64 over a
 tree of depth < 64 (error < 2^-46 sum |vhat w|); the update's per-block fixed point of h_i 2^{q_ib}
-keeps 54 bits of the largest term. The tolerances below are those bounds with a factor-4 margin.
+keeps 54 bits of the largest term, and each of its at most 2 ceil(nvec/32) integer roundings (a
+group sum, a rescaling to a larger block scale) is below 2^(gb-58) of the largest possible term,
+2^gb >= ceil(nvec/32). The tolerances below are those bounds with a factor-4 margin.
 """
 import numpy as np
 import pytest
