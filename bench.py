@@ -251,6 +251,86 @@ def time_to_tol(pkg, torch, device, repeats=3):
     return out
 
 
+def serving(pkg, torch, device, count: int, n_min: float, n_max: float, budget_gb: float = 96.0,
+            max_active: int = 16, steps_per_turn: int = 8, restart: int = 100, seed: int = 3):
+    """The serving workload: a Poisson stream of convection-diffusion solves (n log-uniform in
+    [n_min, n_max], 2D/3D, Pe in [1, 100], tol in {1e-8, 1e-10, 1e-12}, basis format uniform over
+    the seven storage formats), served by the library's runtime (cbg_server_*) within an HBM
+    budget. The arrival rate is 0.8 of the capacity measured with every request submitted at once.
+    The baseline is sequential fp64-basis GMRES: each request's own solve time with the fp64
+    basis (context creation excluded), replayed through a FIFO queue with the same arrivals."""
+    import workloads
+
+    reqs = workloads.serving_mix(count, 1.0, seed=seed, n_min=n_min, n_max=n_max)
+    cases = []
+    for r in reqs:
+        A = workloads.convdiff(r.N, r.dim, r.wind, r.peclet, device=device)
+        xt = workloads.uniform_vector(A.n, 1000 + r.rid, device=device)
+        b = pkg.spmv(A.row_ptr, A.col, A.vals, xt).clone()
+        o = pkg.default_opts(restart=min(restart, A.n), fmt=r.fmt, frsz2_bits=r.frsz2_bits, tol=r.tol,
+                             max_iters=20000)
+        cases.append((r, A, b, o))
+    torch.cuda.synchronize()
+
+    def run(arrivals):
+        srv = pkg.Server(int(budget_gb * 1e9), max_active=max_active, steps_per_turn=steps_per_turn, max_bypass=8)
+        xs = [torch.zeros(A.n, dtype=torch.float64, device=device) for _, A, _, _ in cases]
+        done, nxt = {}, 0
+        t0 = srv.clock()
+        while len(done) < len(cases):
+            now = srv.clock() - t0
+            while nxt < len(cases) and arrivals[nxt] <= now:
+                r, A, b, o = cases[nxt]
+                srv.submit(nxt, A.row_ptr, A.col, A.vals, b, xs[nxt], o)
+                nxt += 1
+            for c in srv.poll():
+                done[c.tag] = c
+        srv.close()
+        lat = np.array([done[i].t_done - t0 - arrivals[i] for i in range(len(cases))])
+        span = max(c.t_done for c in done.values()) - t0 - arrivals[0]
+        ok = sum(1 for c in done.values() if c.status == 0 and c.result.converged)
+        return lat, span, ok
+
+    # capacity: everything submitted at t = 0
+    lat0, span0, _ = run(np.zeros(len(cases)))
+    capacity = len(cases) / span0
+    rate = 0.8 * capacity
+    arrivals = np.array([r.arrival_s for r, _, _, _ in cases]) / rate
+    lat, span, ok = run(arrivals)
+    # sequential fp64-basis GMRES: per-request solve time, then a FIFO queue over the same arrivals
+    service = []
+    for r, A, b, o in cases:
+        o64 = pkg.default_opts(restart=o.restart, fmt="fp64", tol=o.tol, max_iters=20000)
+        S = pkg.Solver(A.row_ptr, A.col, A.vals, opts=o64)
+        x = torch.zeros(A.n, dtype=torch.float64, device=device)
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        S.solve(b, x)
+        torch.cuda.synchronize()
+        service.append(time.perf_counter() - t)
+        S.close()
+    fin, seq_lat = 0.0, []
+    for a, sv in zip(arrivals, service):
+        fin = max(fin, a) + sv
+        seq_lat.append(fin - a)
+    seq_lat = np.array(seq_lat)
+    ns = [A.n for _, A, _, _ in cases]
+    return {"requests": len(cases), "served_converged": ok,
+            "n_range": [int(min(ns)), int(max(ns))], "n_log_uniform": [n_min, n_max],
+            "capacity_solves_per_s": capacity, "arrival_rate_per_s": rate,
+            "p50_latency_s": float(np.percentile(lat, 50)), "p99_latency_s": float(np.percentile(lat, 99)),
+            "solves_per_s": len(cases) / span,
+            "sequential_fp64": {"p50_latency_s": float(np.percentile(seq_lat, 50)),
+                                "p99_latency_s": float(np.percentile(seq_lat, 99)),
+                                "solves_per_s": len(cases) / (fin - arrivals[0]),
+                                "capacity_solves_per_s": len(cases) / sum(service)},
+            "server": {"hbm_budget_gb": budget_gb, "max_active": max_active, "steps_per_turn": steps_per_turn,
+                       "restart": restart},
+            "config": "Poisson arrivals at 0.8 x measured capacity; 2D/3D convection-diffusion 50/50, Pe U[1,100], "
+                      "wind ones; tol {1e-8,1e-10,1e-12}; basis format uniform over fp64/fp32/fp16/bf16/frsz2_16/21/32;"
+                      " b = A x, x U[-1,1]; seed 3"}
+
+
 # ------------------------------------------------------------------------------------------------
 # Oracle (CPU) arm
 # ------------------------------------------------------------------------------------------------
@@ -320,6 +400,8 @@ def main():
     ap.add_argument("--fmt", default="frsz2")
     ap.add_argument("--bits", type=int, default=32)
     ap.add_argument("--no-extras", action="store_true", help="skip the format sweep, e2e, solve and CPU legs")
+    ap.add_argument("--serving-requests", type=int, default=100, help="requests of the serving leg (0 skips it)")
+    ap.add_argument("--serving-nmax", type=float, default=1e6, help="largest request n of the serving leg")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -430,6 +512,8 @@ def main():
         fmts["speedup_frsz2_32_vs_fp64_per_step"] = fmts["fp64"]["ms_per_step"] / fmts["frsz2_32"]["ms_per_step"]
         line["formats"] = fmts
         line["time_to_tol"] = time_to_tol(pkg, torch, device)
+        if args.serving_requests > 0:
+            line["serving"] = serving(pkg, torch, device, args.serving_requests, 1e4, args.serving_nmax)
         line["cpu_baseline"] = cpu_baseline(args.n, args.nvec)
     if dist:
         dist.barrier()

@@ -194,10 +194,83 @@ int cbgmres_solve(cbg_ctx* ctx, const double* d_b, double* d_x, cbg_result* resu
  *   cbgmres_advance  runs up to max_steps further Arnoldi steps, restarts included, and reports
  *                    in *done whether the solve has finished (converged, failed or out of steps);
  *   cbgmres_finish   fills the result and returns the solve's status.
- * b and x must stay valid from start to finish. advance synchronises at the end of each cycle. */
+ * b and x must stay valid from start to finish. advance never waits on the device: at the end of
+ * each cycle it polls an event and returns CBG_OK with *done = 0 until the restart's residual
+ * is on the host. */
 int cbgmres_start(cbg_ctx* ctx, const double* d_b, double* d_x);
 int cbgmres_advance(cbg_ctx* ctx, int32_t max_steps, int32_t* done);
 int cbgmres_finish(cbg_ctx* ctx, cbg_result* result);
+
+/* ---- Serving runtime: continuous batching of many solves on one GPU -------------------------
+ *
+ * A server owns one block of device memory (the HBM budget), one CUDA stream per slot and the
+ * pinned control blocks of its slots. Requests are queued by cbg_server_submit without GPU work.
+ * Every cbg_server_poll is one scheduling turn:
+ *   1. each admitted solve is advanced by up to steps_per_turn Arnoldi steps on its own stream
+ *      (cbgmres_advance; at most one earlier turn's work may still be in flight per slot, so the
+ *      host never runs far ahead of the device and never blocks on a full launch queue);
+ *   2. finished solves release their slot and their workspace, and are reported as completions;
+ *   3. queued requests are admitted in arrival order while a slot is free and their workspace
+ *      (cbgmres_workspace_bytes) fits in the free budget. A request that does not fit is
+ *      passed by later ones until it has been passed max_bypass times; then admission stops
+ *      until it fits, so a large request is never starved.
+ * Admission clears the workspace and validates the matrix on the slot's stream; the solve starts
+ * on a later turn, once that validation has run (a bad matrix completes with
+ * CBG_ERR_BAD_MATRIX and no SpMV ever reads it). Solves of different slots overlap on the
+ * device. A solve's arithmetic is the same as cbgmres_solve's: the result does not depend on
+ * the other requests in flight.
+ *
+ * Nothing in a turn waits on the device, allocates or frees device memory, or synchronises
+ * the device. The matrix, b and x of a request are caller-owned device memory that must stay
+ * valid until its completion is returned; x holds x0 on entry and the solution on completion. */
+typedef struct cbg_server cbg_server;
+
+typedef struct {
+  uint64_t tag;                 /* caller's identifier, returned in the completion */
+  int32_t n;
+  int64_t nnz;
+  const int32_t* d_row_ptr;     /* CSR, as for cbgmres_create */
+  const int32_t* d_col;
+  const double* d_vals;
+  const double* d_b;
+  double* d_x;                  /* in: x0, out: solution */
+  cbg_opts opts;
+} cbg_request;
+
+typedef struct {
+  uint64_t tag;
+  int32_t status;               /* CBG_OK, CBG_ERR_NOT_CONVERGED, CBG_ERR_BAD_MATRIX, ... */
+  cbg_result result;            /* valid when status is CBG_OK or CBG_ERR_NOT_CONVERGED */
+  double t_submit;              /* seconds on the server clock (cbg_server_clock) */
+  double t_admit;               /* workspace reserved and validation enqueued */
+  double t_done;                /* completion observed by the server */
+} cbg_completion;
+
+/* hbm_budget: bytes of device memory the server reserves (one cudaMalloc, at create);
+ * max_active: concurrent solves (slots, streams), 1..256; steps_per_turn >= 1;
+ * max_bypass >= 0. Errors: CBG_ERR_INVALID_ARG, CBG_ERR_OOM, CBG_ERR_CUDA. */
+int cbg_server_create(cbg_server** out, size_t hbm_budget, int32_t max_active, int32_t steps_per_turn,
+                      int32_t max_bypass);
+
+/* Queues a request (the struct is copied). CBG_ERR_INVALID_ARG for invalid options or CSR
+ * arguments, CBG_ERR_OOM when its workspace alone exceeds the budget. No GPU work. */
+int cbg_server_submit(cbg_server* server, const cbg_request* request);
+
+/* One scheduling turn. Writes up to cap completions to out[0..*n_out); completions beyond cap
+ * are kept for the next call. */
+int cbg_server_poll(cbg_server* server, cbg_completion* out, int32_t cap, int32_t* n_out);
+
+/* Requests admitted and not yet completed, requests queued, completions not yet returned, and
+ * bytes of the budget in use. Any output pointer may be NULL. */
+int cbg_server_stats(const cbg_server* server, int32_t* active, int32_t* queued, int32_t* pending,
+                     size_t* bytes_in_use);
+
+/* Seconds since the server was created (steady clock); the time base of the completions. */
+double cbg_server_clock(const cbg_server* server);
+
+/* Waits for every slot's stream and frees the server. Requests still queued or in flight are
+ * dropped (their x is unspecified). Accepts NULL. */
+int cbg_server_destroy(cbg_server* server);
 
 /* Copies up to cap recorded implicit relative residuals (opts.history != 0) to h_out. */
 int cbgmres_history(cbg_ctx* ctx, double* h_out, int64_t cap, int64_t* count);

@@ -27,7 +27,8 @@ EXPORTS = ["cbg_frsz2_bytes", "cbg_frsz2_compress", "cbg_frsz2_decompress", "cbg
            "cbg_csr_validate",
            "cbg_spmv_work_bytes", "cbg_spmv", "cbg_opts_default", "cbgmres_workspace_bytes", "cbgmres_create",
            "cbgmres_solve", "cbgmres_start", "cbgmres_advance", "cbgmres_finish", "cbgmres_history",
-           "cbgmres_destroy", "cbg_last_error", "cbg_version"]
+           "cbgmres_destroy", "cbg_server_create", "cbg_server_submit", "cbg_server_poll", "cbg_server_stats",
+           "cbg_server_clock", "cbg_server_destroy", "cbg_last_error", "cbg_version"]
 
 
 class CbgError(RuntimeError):
@@ -46,6 +47,17 @@ class Result(ctypes.Structure):
     _fields_ = [("iters", ctypes.c_int64), ("restarts", ctypes.c_int64), ("reorths", ctypes.c_int64),
                 ("converged", ctypes.c_int32), ("status", ctypes.c_int32), ("true_rrn", ctypes.c_double),
                 ("implicit_rrn", ctypes.c_double), ("seconds", ctypes.c_double)]
+
+
+class Request(ctypes.Structure):
+    _fields_ = [("tag", ctypes.c_uint64), ("n", ctypes.c_int32), ("nnz", ctypes.c_int64),
+                ("d_row_ptr", ctypes.c_void_p), ("d_col", ctypes.c_void_p), ("d_vals", ctypes.c_void_p),
+                ("d_b", ctypes.c_void_p), ("d_x", ctypes.c_void_p), ("opts", Opts)]
+
+
+class Completion(ctypes.Structure):
+    _fields_ = [("tag", ctypes.c_uint64), ("status", ctypes.c_int32), ("result", Result),
+                ("t_submit", ctypes.c_double), ("t_admit", ctypes.c_double), ("t_done", ctypes.c_double)]
 
 
 class Basis(ctypes.Structure):
@@ -99,6 +111,13 @@ def load(path: str | None = None):
         "cbgmres_finish": (c_int, [P, ctypes.POINTER(Result)]),
         "cbgmres_history": (c_int, [P, P, i64, ctypes.POINTER(i64)]),
         "cbgmres_destroy": (c_int, [P]),
+        "cbg_server_create": (c_int, [ctypes.POINTER(P), sz, i32, i32, i32]),
+        "cbg_server_submit": (c_int, [P, ctypes.POINTER(Request)]),
+        "cbg_server_poll": (c_int, [P, ctypes.POINTER(Completion), i32, ctypes.POINTER(i32)]),
+        "cbg_server_stats": (c_int, [P, ctypes.POINTER(i32), ctypes.POINTER(i32), ctypes.POINTER(i32),
+                                     ctypes.POINTER(sz)]),
+        "cbg_server_clock": (ctypes.c_double, [P]),
+        "cbg_server_destroy": (c_int, [P]),
         "cbg_last_error": (ctypes.c_char_p, []),
         "cbg_version": (ctypes.c_char_p, []),
     }
@@ -332,6 +351,75 @@ class Solver:
         if getattr(self, "handle", None):
             lib().cbgmres_destroy(self.handle)
             self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+# ---------------------------------------------------------------------------------------------
+# Serving runtime
+# ---------------------------------------------------------------------------------------------
+
+@dataclass
+class ServedSolve:
+    tag: int
+    status: int
+    result: SolveResult
+    t_submit: float
+    t_admit: float
+    t_done: float
+
+    @property
+    def latency(self) -> float:
+        return self.t_done - self.t_submit
+
+
+class Server:
+    """The library's serving runtime (cbg_server_*): continuous batching of solves within an HBM
+    budget. Tensors of a request are kept referenced here until its completion is returned."""
+
+    def __init__(self, hbm_budget: int, max_active: int = 16, steps_per_turn: int = 8, max_bypass: int = 8):
+        h = ctypes.c_void_p(None)
+        check(lib().cbg_server_create(ctypes.byref(h), int(hbm_budget), max_active, steps_per_turn, max_bypass))
+        self.handle = h
+        self._inflight = {}
+        self._buf = (Completion * 64)()
+
+    def clock(self) -> float:
+        return float(lib().cbg_server_clock(self.handle))
+
+    def submit(self, tag: int, row_ptr: torch.Tensor, col: torch.Tensor, vals: torch.Tensor, b: torch.Tensor,
+               x: torch.Tensor, opts: Opts):
+        r = Request(tag=tag, n=row_ptr.numel() - 1, nnz=col.numel(), d_row_ptr=_ptr(row_ptr).value,
+                    d_col=_ptr(col).value, d_vals=_ptr(vals).value, d_b=_ptr(b).value, d_x=_ptr(x).value, opts=opts)
+        check(lib().cbg_server_submit(self.handle, ctypes.byref(r)))
+        self._inflight[tag] = (row_ptr, col, vals, b, x)
+
+    def poll(self) -> list[ServedSolve]:
+        out = []
+        while True:
+            k = ctypes.c_int32(0)
+            check(lib().cbg_server_poll(self.handle, self._buf, len(self._buf), ctypes.byref(k)))
+            for i in range(k.value):
+                c = self._buf[i]
+                self._inflight.pop(c.tag, None)
+                out.append(ServedSolve(c.tag, c.status, _result(c.result), c.t_submit, c.t_admit, c.t_done))
+            if k.value < len(self._buf):
+                return out
+
+    def stats(self):
+        a, q, p, u = ctypes.c_int32(0), ctypes.c_int32(0), ctypes.c_int32(0), ctypes.c_size_t(0)
+        check(lib().cbg_server_stats(self.handle, ctypes.byref(a), ctypes.byref(q), ctypes.byref(p), ctypes.byref(u)))
+        return {"active": a.value, "queued": q.value, "pending": p.value, "bytes_in_use": u.value}
+
+    def close(self):
+        if getattr(self, "handle", None):
+            lib().cbg_server_destroy(self.handle)
+            self.handle = None
+            self._inflight.clear()
 
     def __del__(self):
         try:

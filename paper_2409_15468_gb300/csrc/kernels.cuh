@@ -112,4 +112,14 @@ struct GivensArgs {
 int launch_givens(const GivensArgs& a, int j, cudaStream_t stream);
 int launch_cycle_init(SolverCtl* ctl, double* g, int m, int steps_allowed, cudaStream_t stream);
 
+// ---- solver contexts over caller-provided memory (solver.cu), used by the serving runtime ----
+size_t ctx_pinned_bytes();
+size_t ctx_device_bytes(int32_t n, const cbg_opts* opts);
+int ctx_create_in(cbg_ctx** out, int32_t n, int64_t nnz, const int32_t* d_row_ptr, const int32_t* d_col,
+                  const double* d_vals, const cbg_opts* opts, cudaStream_t stream, void* dmem, size_t dbytes,
+                  void* pinned);
+int ctx_validated(cbg_ctx* c);
+void ctx_release(cbg_ctx* c);
+cudaStream_t ctx_stream(const cbg_ctx* c);
+
 }  // namespace cbg

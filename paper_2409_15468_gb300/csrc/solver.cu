@@ -148,7 +148,7 @@ using namespace cbg;
 
 namespace {
 
-enum Phase { kIdle = 0, kWaitResidual = 1, kInCycle = 2, kDone = 3 };
+enum Phase { kValidating = -1, kIdle = 0, kWaitResidual = 1, kInCycle = 2, kDone = 3 };
 
 int64_t round_up(int64_t v, int64_t a) { return (v + a - 1) / a * a; }
 
@@ -162,9 +162,11 @@ struct cbg_ctx {
   const double* vals;
   cbg_opts opts;
   cudaStream_t stream;
-  // device workspace (one allocation)
+  // device workspace (one block) and pinned control-block mirror; owned unless provided by a server
   void* dmem;
   size_t dbytes;
+  bool owns_dmem;
+  bool owns_pinned;
   BasisMut basis;
   double *v, *w, *H, *R, *cs, *sn, *g, *u, *y, *partials, *hist, *bnorm2;
   SolverCtl* ctl;
@@ -389,6 +391,131 @@ int after_residual(cbg_ctx* c) {
 
 }  // namespace
 
+namespace cbg {
+
+size_t ctx_pinned_bytes() { return (sizeof(SolverCtl) + 64 + 255) / 256 * 256; }
+
+size_t ctx_device_bytes(int32_t n, const cbg_opts* opts) { return opts_valid(n, opts) ? layout_of(n, opts).total : 0; }
+
+// A context over caller-provided memory: dbytes >= ctx_device_bytes(n, opts) of device memory
+// (256-byte aligned) and ctx_pinned_bytes() of pinned host memory. Nothing is allocated but the
+// host object and an event, and nothing waits: the workspace is cleared and the CSR validated on
+// `stream`, and ctx_validated() reports the outcome once that work has run.
+int ctx_create_in(cbg_ctx** out, int32_t n, int64_t nnz, const int32_t* d_row_ptr, const int32_t* d_col,
+                  const double* d_vals, const cbg_opts* opts, cudaStream_t stream, void* dmem, size_t dbytes,
+                  void* pinned) {
+  *out = nullptr;
+  if (!opts_valid(n, opts)) {
+    set_error("cbgmres_create: invalid n or options (1 <= restart <= min(n, 1024), tol > 0, l in {16,21,32})");
+    return CBG_ERR_INVALID_ARG;
+  }
+  if (nnz < 0 || nnz > INT32_MAX || !d_row_ptr || (nnz > 0 && (!d_col || !d_vals))) {
+    set_error("cbgmres_create: invalid CSR arguments");
+    return CBG_ERR_INVALID_ARG;
+  }
+  const Layout L = layout_of(n, opts);
+  if (!dmem || dbytes < L.total || reinterpret_cast<uintptr_t>(dmem) % 256 || !pinned) {
+    set_error("cbgmres_create: workspace too small or misaligned");
+    return CBG_ERR_INVALID_ARG;
+  }
+  DeviceInfo di;
+  int st = device_info(&di);
+  if (st) return st;
+  cbg_ctx* c = new (std::nothrow) cbg_ctx();
+  if (!c) {
+    set_error("cbgmres_create: host allocation failed");
+    return CBG_ERR_OOM;
+  }
+  c->n = n;
+  c->nnz = nnz;
+  c->row_ptr = d_row_ptr;
+  c->col = d_col;
+  c->vals = d_vals;
+  c->opts = *opts;
+  if (c->opts.fmt != CBG_FRSZ2) c->opts.frsz2_bits = 32;
+  c->stream = stream;
+  c->dmem = dmem;
+  c->dbytes = L.total;
+  c->owns_dmem = false;
+  c->owns_pinned = false;
+  uint8_t* base = static_cast<uint8_t*>(c->dmem);
+  c->basis.vals = base + L.off_basis_vals;
+  c->basis.vstride = L.vstride;
+  c->basis.exps = reinterpret_cast<uint32_t*>(base + L.off_basis_exps);
+  c->basis.estride = L.estride;
+  c->basis.n = n;
+  c->basis.fmt = c->opts.fmt;
+  c->basis.l = c->opts.frsz2_bits;
+  c->v = reinterpret_cast<double*>(base + L.off_v);
+  c->w = reinterpret_cast<double*>(base + L.off_w);
+  c->H = reinterpret_cast<double*>(base + L.off_H);
+  c->R = reinterpret_cast<double*>(base + L.off_R);
+  c->cs = reinterpret_cast<double*>(base + L.off_cs);
+  c->sn = reinterpret_cast<double*>(base + L.off_sn);
+  c->g = reinterpret_cast<double*>(base + L.off_g);
+  c->u = reinterpret_cast<double*>(base + L.off_u);
+  c->y = reinterpret_cast<double*>(base + L.off_y);
+  c->partials = reinterpret_cast<double*>(base + L.off_partials);
+  c->hist = c->opts.history ? reinterpret_cast<double*>(base + L.off_hist) : nullptr;
+  c->ctl = reinterpret_cast<SolverCtl*>(base + L.off_ctl);
+  c->bnorm2 = reinterpret_cast<double*>(base + L.off_bnorm2);
+  c->ctl_host = static_cast<SolverCtl*>(pinned);
+  c->bnorm2_host = reinterpret_cast<double*>(static_cast<uint8_t*>(pinned) + sizeof(SolverCtl) + 16);
+  cudaError_t e = cudaEventCreateWithFlags(&c->ev, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaMemsetAsync(c->dmem, 0, L.total, c->stream);
+  if (e != cudaSuccess) {
+    st = cuda_fail(e, "cbgmres_create setup");
+    ctx_release(c);
+    return st;
+  }
+  st = launch_validate_csr(n, nnz, d_row_ptr, d_col, &c->ctl->err, c->stream);
+  if (st) {
+    ctx_release(c);
+    return st;
+  }
+  e = cudaMemcpyAsync(c->ctl_host, c->ctl, sizeof(SolverCtl), cudaMemcpyDeviceToHost, c->stream);
+  if (e == cudaSuccess) e = cudaEventRecord(c->ev, c->stream);
+  if (e != cudaSuccess) {
+    st = cuda_fail(e, "cbgmres_create validation");
+    ctx_release(c);
+    return st;
+  }
+  c->phase = kValidating;
+  *out = c;
+  return CBG_OK;
+}
+
+// 1: validated (the context is idle), 0: the validation has not run yet, < 0: CBG_ERR_* (a bad
+// matrix or a CUDA error). Never waits.
+int ctx_validated(cbg_ctx* c) {
+  if (c->phase != kValidating) return 1;
+  cudaError_t q = cudaEventQuery(c->ev);
+  if (q == cudaErrorNotReady) return 0;
+  if (q != cudaSuccess) return cuda_fail(q, "CSR validation");
+  if (c->ctl_host->err & kDevErrBadMatrix) {
+    set_error("cbgmres_create: CSR row pointers not monotone, row_ptr[0] != 0, row_ptr[n] != nnz, or a column "
+              "index outside [0, n)");
+    return CBG_ERR_BAD_MATRIX;
+  }
+  c->phase = kIdle;
+  return 1;
+}
+
+// Waits for the context's stream, then frees what the context owns (not caller-provided memory).
+void ctx_release(cbg_ctx* c) {
+  if (!c) return;
+  cudaStreamSynchronize(c->stream);
+  if (c->owns_dmem && c->dmem) cudaFree(c->dmem);
+  if (c->owns_pinned && c->ctl_host) cudaFreeHost(c->ctl_host);
+  if (c->ev) cudaEventDestroy(c->ev);
+  delete c;
+}
+
+// The stream the context enqueues on.
+cudaStream_t ctx_stream(const cbg_ctx* c) { return c->stream; }
+
+}  // namespace cbg
+
 extern "C" {
 
 int cbg_opts_default(cbg_opts* o) {
@@ -422,84 +549,42 @@ int cbgmres_create(cbg_ctx** out, int32_t n, int64_t nnz, const int32_t* d_row_p
     set_error("cbgmres_create: invalid n or options (1 <= restart <= min(n, 1024), tol > 0, l in {16,21,32})");
     return CBG_ERR_INVALID_ARG;
   }
-  if (nnz < 0 || nnz > INT32_MAX || !d_row_ptr || (nnz > 0 && (!d_col || !d_vals))) {
-    set_error("cbgmres_create: invalid CSR arguments");
-    return CBG_ERR_INVALID_ARG;
-  }
-  DeviceInfo di;
-  int st = device_info(&di);
-  if (st) return st;
-  cbg_ctx* c = new (std::nothrow) cbg_ctx();
-  if (!c) {
-    set_error("cbgmres_create: host allocation failed");
-    return CBG_ERR_OOM;
-  }
-  c->n = n;
-  c->nnz = nnz;
-  c->row_ptr = d_row_ptr;
-  c->col = d_col;
-  c->vals = d_vals;
-  c->opts = *opts;
-  if (c->opts.fmt != CBG_FRSZ2) c->opts.frsz2_bits = 32;
-  c->stream = static_cast<cudaStream_t>(stream);
-  const Layout L = layout_of(n, &c->opts);
-  cudaError_t e = cudaMalloc(&c->dmem, L.total);
+  const size_t total = layout_of(n, opts).total;
+  void* dmem = nullptr;
+  cudaError_t e = cudaMalloc(&dmem, total);
   if (e != cudaSuccess) {
-    delete c;
-    set_error("cbgmres_create: cudaMalloc of %zu bytes failed: %s", L.total, cudaGetErrorString(e));
+    set_error("cbgmres_create: cudaMalloc of %zu bytes failed: %s", total, cudaGetErrorString(e));
     cudaGetLastError();
     return CBG_ERR_OOM;
   }
-  c->dbytes = L.total;
-  uint8_t* base = static_cast<uint8_t*>(c->dmem);
-  c->basis.vals = base + L.off_basis_vals;
-  c->basis.vstride = L.vstride;
-  c->basis.exps = reinterpret_cast<uint32_t*>(base + L.off_basis_exps);
-  c->basis.estride = L.estride;
-  c->basis.n = n;
-  c->basis.fmt = c->opts.fmt;
-  c->basis.l = c->opts.frsz2_bits;
-  c->v = reinterpret_cast<double*>(base + L.off_v);
-  c->w = reinterpret_cast<double*>(base + L.off_w);
-  c->H = reinterpret_cast<double*>(base + L.off_H);
-  c->R = reinterpret_cast<double*>(base + L.off_R);
-  c->cs = reinterpret_cast<double*>(base + L.off_cs);
-  c->sn = reinterpret_cast<double*>(base + L.off_sn);
-  c->g = reinterpret_cast<double*>(base + L.off_g);
-  c->u = reinterpret_cast<double*>(base + L.off_u);
-  c->y = reinterpret_cast<double*>(base + L.off_y);
-  c->partials = reinterpret_cast<double*>(base + L.off_partials);
-  c->hist = c->opts.history ? reinterpret_cast<double*>(base + L.off_hist) : nullptr;
-  c->ctl = reinterpret_cast<SolverCtl*>(base + L.off_ctl);
-  c->bnorm2 = reinterpret_cast<double*>(base + L.off_bnorm2);
-  e = cudaMallocHost(&c->ctl_host, sizeof(SolverCtl) + 64);
-  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev, cudaEventDisableTiming);
-  if (e == cudaSuccess) e = cudaMemsetAsync(c->dmem, 0, L.total, c->stream);
+  void* pinned = nullptr;
+  e = cudaMallocHost(&pinned, ctx_pinned_bytes());
   if (e != cudaSuccess) {
-    st = cuda_fail(e, "cbgmres_create setup");
-    cbgmres_destroy(c);
-    return st;
+    cudaFree(dmem);
+    return cuda_fail(e, "cbgmres_create: pinned control block");
   }
-  c->bnorm2_host = reinterpret_cast<double*>(reinterpret_cast<uint8_t*>(c->ctl_host) + sizeof(SolverCtl) + 16);
-  st = launch_validate_csr(n, nnz, d_row_ptr, d_col, &c->ctl->err, c->stream);
+  cbg_ctx* c = nullptr;
+  int st = ctx_create_in(&c, n, nnz, d_row_ptr, d_col, d_vals, opts, static_cast<cudaStream_t>(stream), dmem, total,
+                         pinned);
   if (st) {
-    cbgmres_destroy(c);
+    cudaFree(dmem);
+    cudaFreeHost(pinned);
     return st;
   }
-  e = cudaMemcpyAsync(c->ctl_host, c->ctl, sizeof(SolverCtl), cudaMemcpyDeviceToHost, c->stream);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  c->owns_dmem = true;
+  c->owns_pinned = true;
+  // wait for the CSR validation enqueued by ctx_create_in
+  e = cudaEventSynchronize(c->ev);
   if (e != cudaSuccess) {
     st = cuda_fail(e, "cbgmres_create validation");
     cbgmres_destroy(c);
     return st;
   }
-  if (c->ctl_host->err & kDevErrBadMatrix) {
-    set_error("cbgmres_create: CSR row pointers not monotone, row_ptr[0] != 0, row_ptr[n] != nnz, or a column "
-              "index outside [0, n)");
+  st = ctx_validated(c);
+  if (st != 1) {
     cbgmres_destroy(c);
-    return CBG_ERR_BAD_MATRIX;
+    return st < 0 ? st : CBG_ERR_CUDA;
   }
-  c->phase = kIdle;
   *out = c;
   return CBG_OK;
 }
@@ -508,6 +593,17 @@ int cbgmres_start(cbg_ctx* c, const double* d_b, double* d_x) {
   if (!c || !d_b || !d_x) {
     set_error("cbgmres_start: null argument");
     return CBG_ERR_INVALID_ARG;
+  }
+  if (c->phase == kValidating) {
+    // a context made over server memory: its matrix must be known valid before any SpMV runs
+    cudaError_t e = cudaEventSynchronize(c->ev);
+    if (e != cudaSuccess) return cuda_fail(e, "CSR validation wait");
+    int v = ctx_validated(c);
+    if (v != 1) return v < 0 ? v : CBG_ERR_CUDA;
+  }
+  if (c->phase != kIdle && c->phase != kDone) {
+    set_error("cbgmres_start: a solve is in progress on this context");
+    return CBG_ERR_STATE;
   }
   c->b = d_b;
   c->x = d_x;
@@ -538,7 +634,7 @@ int cbgmres_advance(cbg_ctx* c, int32_t max_steps, int32_t* done) {
     return CBG_ERR_INVALID_ARG;
   }
   *done = 0;
-  if (c->phase == kIdle) {
+  if (c->phase == kIdle || c->phase == kValidating) {
     set_error("cbgmres_advance: no solve started");
     return CBG_ERR_STATE;
   }
@@ -648,12 +744,7 @@ int cbgmres_history(cbg_ctx* c, double* h_out, int64_t cap, int64_t* count) {
 }
 
 int cbgmres_destroy(cbg_ctx* c) {
-  if (!c) return CBG_OK;
-  cudaStreamSynchronize(c->stream);
-  if (c->dmem) cudaFree(c->dmem);
-  if (c->ctl_host) cudaFreeHost(c->ctl_host);
-  if (c->ev) cudaEventDestroy(c->ev);
-  delete c;
+  ctx_release(c);
   return CBG_OK;
 }
 

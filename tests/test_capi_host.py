@@ -80,3 +80,27 @@ def test_no_cpu_fallback(pkg):
     addr = (ctypes.addressof(buf) + 255) // 256 * 256
     st = L.cbg_frsz2_compress(ctypes.c_void_p(addr), 4, 32, ctypes.c_void_p(addr), ctypes.c_void_p(addr), None)
     assert st == -2  # CBG_ERR_CUDA: no device, and no host path to fall back to
+
+
+def test_server_arguments_rejected(pkg):
+    L = pkg.lib()
+    h = ctypes.c_void_p()
+    assert L.cbg_server_create(None, 1 << 20, 4, 4, 4) == -1
+    assert L.cbg_server_create(ctypes.byref(h), 0, 4, 4, 4) == -1  # budget below one granule
+    assert L.cbg_server_create(ctypes.byref(h), 1 << 20, 0, 4, 4) == -1  # no slot
+    assert L.cbg_server_create(ctypes.byref(h), 1 << 20, 257, 4, 4) == -1
+    assert L.cbg_server_create(ctypes.byref(h), 1 << 20, 4, 0, 4) == -1  # no step per turn
+    assert L.cbg_server_create(ctypes.byref(h), 1 << 20, 4, 4, -1) == -1
+    assert L.cbg_server_submit(None, None) == -1
+    n = ctypes.c_int32(0)
+    assert L.cbg_server_poll(None, None, 0, ctypes.byref(n)) == -1
+    assert L.cbg_server_stats(None, None, None, None, None) == -1
+    assert L.cbg_server_clock(None) == 0.0
+    assert L.cbg_server_destroy(None) == 0
+
+
+@pytest.mark.skipif(torch.cuda.is_available(), reason="checks the behaviour without a CUDA device")
+def test_server_needs_a_device(pkg):
+    h = ctypes.c_void_p()
+    assert pkg.lib().cbg_server_create(ctypes.byref(h), 1 << 20, 4, 4, 4) == -2
+    assert not h.value
