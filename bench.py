@@ -251,6 +251,52 @@ def time_to_tol(pkg, torch, device, repeats=3):
     return out
 
 
+def solve_c3(pkg, torch, device, formats, N: int = 256, restart: int = 100, tol: float = 1e-10,
+             max_iters: int = 20000, verify: bool = True):
+    """Full CB-GMRES(restart) solves on the 3D 7-point convection-diffusion system on an N^3 grid
+    (wind (1,1,1), Peclet 50, b = A 1, x0 = 0) to a relative residual of tol, one per basis
+    format, through cbgmres_solve with device-resident b and x. Each final x is checked on the
+    host with the oracle's SpMV and compensated dot: ||b - A x|| / ||b|| recomputed independently
+    of the GPU path."""
+    import workloads
+
+    A = workloads.convdiff(N, 3, (1.0, 1.0, 1.0), 50.0, device=device)
+    b = pkg.spmv(A.row_ptr, A.col, A.vals, torch.ones(A.n, dtype=torch.float64, device=device)).clone()
+    host = None
+    if verify:
+        import oracle
+
+        oracle.build()
+        rp, col, vals = A.numpy()
+        bh = b.cpu().numpy()
+        host = (oracle, rp, col, vals, bh, oracle.nrm2(bh))
+    out = {"config": f"3D 7-point convection-diffusion {N}^3 (n={A.n}, nnz={A.nnz}), wind (1,1,1)*50, b = A*1, "
+                     f"x0 = 0, restart {restart}, tol {tol}, max_iters {max_iters}"}
+    for f in formats:
+        fmt, bits = (f.split("_")[0], int(f.split("_")[1])) if f.startswith("frsz2") else (f, 32)
+        S = pkg.Solver(A.row_ptr, A.col, A.vals, restart=restart, tol=tol, fmt=fmt, frsz2_bits=bits,
+                       max_iters=max_iters)
+        x = torch.zeros(A.n, dtype=torch.float64, device=device)
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        r = S.solve(b, x)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t
+        S.close()
+        res = {"seconds": dt, "iters": r.iters, "restarts": r.restarts, "reorths": r.reorths,
+               "converged": r.converged, "true_rrn": r.true_rrn, "ms_per_iter": 1e3 * dt / max(r.iters, 1)}
+        if host:
+            orc, rp, col, vals, bh, bn = host
+            xh = x.cpu().numpy()
+            res["oracle_checked_rrn"] = orc.nrm2(bh - orc.spmv(rp, col, vals, xh)) / bn
+        out[f] = res
+        del x
+        torch.cuda.empty_cache()
+    if "fp64" in out and "frsz2_32" in out:
+        out["speedup_frsz2_32_vs_fp64"] = out["fp64"]["seconds"] / out["frsz2_32"]["seconds"]
+    return out
+
+
 def serving(pkg, torch, device, count: int, n_min: float, n_max: float, budget_gb: float = 96.0,
             max_active: int = 16, steps_per_turn: int = 8, restart: int = 100, seed: int = 3):
     """The serving workload: a Poisson stream of convection-diffusion solves (n log-uniform in
@@ -402,6 +448,8 @@ def main():
     ap.add_argument("--no-extras", action="store_true", help="skip the format sweep, e2e, solve and CPU legs")
     ap.add_argument("--serving-requests", type=int, default=100, help="requests of the serving leg (0 skips it)")
     ap.add_argument("--serving-nmax", type=float, default=1e6, help="largest request n of the serving leg")
+    ap.add_argument("--solve-c3", default="", help="comma-separated basis formats (fp64, fp32, fp16, bf16, "
+                    "frsz2_16, frsz2_21, frsz2_32): run only the full 256^3 solves to 1e-10 and print them")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -444,6 +492,13 @@ def main():
     device = torch.device("cuda", local if world > 1 else torch.cuda.current_device())
     torch.cuda.set_device(device)
     peak, peak_src = load_peaks()
+    if args.solve_c3:
+        if rank == 0:
+            print(json.dumps({"solve_c3": solve_c3(pkg, torch, device, args.solve_c3.split(","))}))
+        if dist:
+            dist.barrier()
+            dist.destroy_process_group()
+        return
     fmt, l = args.fmt, args.bits
     B, w = make_basis(pkg, torch, fmt, l, args.n, args.nvec, device)
     sb = step_bytes(fmt, l, args.n, args.nvec)
@@ -512,6 +567,7 @@ def main():
         fmts["speedup_frsz2_32_vs_fp64_per_step"] = fmts["fp64"]["ms_per_step"] / fmts["frsz2_32"]["ms_per_step"]
         line["formats"] = fmts
         line["time_to_tol"] = time_to_tol(pkg, torch, device)
+        line["time_to_tol_c3"] = solve_c3(pkg, torch, device, ["frsz2_32", "fp64"])
         if args.serving_requests > 0:
             line["serving"] = serving(pkg, torch, device, args.serving_requests, 1e4, args.serving_nmax)
         line["cpu_baseline"] = cpu_baseline(args.n, args.nvec)
