@@ -101,7 +101,7 @@ def load(path: str | None = None):
         "cbg_basis_update": (c_int, [ctypes.POINTER(Basis), i32, P, P, P, P, sz, P]),
         "cbg_csr_validate": (c_int, [i32, i64, P, P, P]),
         "cbg_spmv_work_bytes": (sz, [i32]),
-        "cbg_spmv": (c_int, [i32, P, P, P, P, P, P, P, sz, P]),
+        "cbg_spmv": (c_int, [i32, i64, P, P, P, P, P, P, P, sz, P]),
         "cbg_opts_default": (c_int, [ctypes.POINTER(Opts)]),
         "cbgmres_workspace_bytes": (sz, [i32, ctypes.POINTER(Opts)]),
         "cbgmres_create": (c_int, [ctypes.POINTER(P), i32, i64, P, P, P, ctypes.POINTER(Opts), P]),
@@ -265,7 +265,7 @@ def spmv(row_ptr: torch.Tensor, col: torch.Tensor, vals: torch.Tensor, x: torch.
     if y is None:
         y = torch.empty(max(n, 1), dtype=torch.float64, device=x.device)
     work = _empty(lib().cbg_spmv_work_bytes(n), x.device)
-    check(lib().cbg_spmv(n, _ptr(row_ptr), _ptr(col), _ptr(vals), _ptr(x), _ptr(y), _ptr(norm2), _ptr(work),
+    check(lib().cbg_spmv(n, col.numel(), _ptr(row_ptr), _ptr(col), _ptr(vals), _ptr(x), _ptr(y), _ptr(norm2), _ptr(work),
                          work.numel(), _stream(stream)))
     return y[:n]
 

@@ -326,11 +326,11 @@ size_t cbg_spmv_work_bytes(int32_t n) {
   return partial_bytes(1) + 256;
 }
 
-int cbg_spmv(int32_t n, const int32_t* d_row_ptr, const int32_t* d_col, const double* d_vals, const double* d_x,
-             double* d_y, double* d_norm2, void* d_work, size_t work_bytes, void* stream) {
-  if (n < 0) return bad("cbg_spmv: negative n");
+int cbg_spmv(int32_t n, int64_t nnz, const int32_t* d_row_ptr, const int32_t* d_col, const double* d_vals,
+             const double* d_x, double* d_y, double* d_norm2, void* d_work, size_t work_bytes, void* stream) {
+  if (n < 0 || nnz < 0 || nnz > INT32_MAX) return bad("cbg_spmv: negative n or nnz outside [0, 2^31)");
   if (n == 0) return CBG_OK;
-  if (!d_row_ptr || !d_x || !d_y) return bad("cbg_spmv: null pointer");
+  if (!d_row_ptr || !d_x || !d_y || (nnz > 0 && (!d_col || !d_vals))) return bad("cbg_spmv: null pointer");
   DeviceInfo di;
   int st = device_info(&di);
   if (st) return st;
@@ -339,7 +339,7 @@ int cbg_spmv(int32_t n, const int32_t* d_row_ptr, const int32_t* d_col, const do
   st = take_work(d_work, work_bytes, 1, s, &w);
   if (st) return st;
   NormEpilogue epi{d_norm2, nullptr, kEpiNone};
-  return launch_spmv(n, d_row_ptr, d_col, d_vals, d_x, d_y, nullptr, w.partials, w.counter, w.err, epi,
+  return launch_spmv(n, nnz, d_row_ptr, d_col, d_vals, d_x, d_y, nullptr, w.partials, w.counter, w.err, epi,
                      Gate{nullptr, nullptr}, s);
 }
 

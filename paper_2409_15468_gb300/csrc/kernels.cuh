@@ -87,9 +87,9 @@ int launch_load(const BasisView& B, int slot, double* dst, cudaStream_t stream);
 
 // ---- spmv.cu ------------------------------------------------------------------------------------
 // y = A x (or y = bsub - A x when bsub is not null); ||y||^2 to the epilogue. partials: kMaxGrid.
-int launch_spmv(int n, const int32_t* row_ptr, const int32_t* col, const double* vals, const double* x, double* y,
-                const double* bsub, double* partials, unsigned int* counter, int* err, const NormEpilogue& epi,
-                const Gate& gate, cudaStream_t stream);
+int launch_spmv(int n, int64_t nnz, const int32_t* row_ptr, const int32_t* col, const double* vals, const double* x,
+                double* y, const double* bsub, double* partials, unsigned int* counter, int* err,
+                const NormEpilogue& epi, const Gate& gate, cudaStream_t stream);
 int launch_validate_csr(int n, int64_t nnz, const int32_t* row_ptr, const int32_t* col, int* err,
                         cudaStream_t stream);
 int launch_sumsq(const double* x, int64_t n, double* partials, unsigned int* counter, int* err, double* out,

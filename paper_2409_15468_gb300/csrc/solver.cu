@@ -273,7 +273,7 @@ GivensArgs givens_args(cbg_ctx* c) {
 // and an event the host polls.
 int enqueue_residual(cbg_ctx* c) {
   NormEpilogue epi{nullptr, c->ctl, kEpiResidual};
-  int st = launch_spmv(c->n, c->row_ptr, c->col, c->vals, c->x, c->w, c->b, c->partials,
+  int st = launch_spmv(c->n, c->nnz, c->row_ptr, c->col, c->vals, c->x, c->w, c->b, c->partials,
                        &c->ctl->counters[kCtrSpmv], &c->ctl->err, epi, Gate{nullptr, nullptr}, c->stream);
   if (st) return st;
   cudaError_t e = cudaMemcpyAsync(c->ctl_host, c->ctl, sizeof(SolverCtl), cudaMemcpyDeviceToHost, c->stream);
@@ -293,7 +293,7 @@ int enqueue_step(cbg_ctx* c, int j) {
   double* hcol = c->H + (size_t)j * ld;
   int st;
   NormEpilogue e_omega{nullptr, ctl, kEpiOmega};
-  st = launch_spmv(c->n, c->row_ptr, c->col, c->vals, c->v, c->w, nullptr, c->partials, &ctl->counters[kCtrSpmv],
+  st = launch_spmv(c->n, c->nnz, c->row_ptr, c->col, c->vals, c->v, c->w, nullptr, c->partials, &ctl->counters[kCtrSpmv],
                    &ctl->err, e_omega, run, c->stream);
   if (st) return st;
   st = launch_basis_dot(B, j + 1, c->w, hcol, c->partials, &ctl->counters[kCtrDot], &ctl->err, run, c->stream);

@@ -3,10 +3,11 @@
 // solver is created. The SpMV reads the uncompressed FP64 vector v: the paper highlights only the
 // basis accesses as compressed.
 //
-// One thread per row: the stencil matrices have ~7 nonzeros per row, so the rows of a warp cover a
-// contiguous stretch of the value and column arrays that L1 serves to the per-nonzero loads, and
-// the FP64 work is exactly one FMA per nonzero (GB300's FP64 rate is the other bound of this
-// kernel). Rows are strided over a grid sized to the SM count so that the norm partials stay few.
+// One thread per row for short rows: the stencil matrices have ~7 nonzeros per row, so the rows of a
+// warp cover a contiguous stretch of the value and column arrays that L1 serves to the per-nonzero
+// loads, and the FP64 work is exactly one FMA per nonzero (GB300's FP64 rate is the other bound of
+// this kernel). Matrices with long rows (mean >= 12 nonzeros) use G lanes per row instead.
+// Rows are strided over a grid sized to the SM count so that the norm partials stay few.
 #include "common.cuh"
 #include "kernels.cuh"
 
@@ -38,6 +39,91 @@ __global__ void __launch_bounds__(256) k_spmv(int n, const int32_t* __restrict__
     if (bsub) s = bsub[i] - s;
     y[i] = s;
     nrm = fma(s, s, nrm);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) nrm += __shfl_xor_sync(0xffffffffu, nrm, o);
+  if (lane == 0) red[warp] = nrm;
+  __syncthreads();
+  if (t == 0) {
+    double s = 0.0;
+    for (int i = 0; i < 8; ++i) s += red[i];
+    partials[blockIdx.x] = s;
+  }
+  if (arrive_last(counter, gridDim.x, &flag)) {
+    if (warp == 0) {
+      const double s = warp_sum_strided(partials, gridDim.x, 1);
+      if (lane == 0) norm_epilogue(epi, s, err);
+    }
+    if (t == 0) *counter = 0;
+  }
+}
+
+// Rows with many nonzeros (power-law matrices): G consecutive lanes per row, so the loads of a
+// row's values and column indices are coalesced and a long row is split G ways. Each lane issues
+// U independent (column, value, x-gather) loads before it uses any of them, and the next row's
+// bounds are loaded before the current row is processed: the kernel is bound by load latency,
+// so it keeps several gathers in flight per lane. The lane's U partial sums and the G lanes of a
+// row are combined in a fixed order (deterministic).
+template <int G, int U>
+__global__ void __launch_bounds__(256) k_spmv_vec(int n, const int32_t* __restrict__ row_ptr,
+                                                  const int32_t* __restrict__ col, const double* __restrict__ vals,
+                                                  const double* __restrict__ x, double* __restrict__ y,
+                                                  const double* __restrict__ bsub, double* __restrict__ partials,
+                                                  unsigned int* counter, int* err, NormEpilogue epi, Gate gate) {
+  if (gate_skip_s(gate)) return;
+  __shared__ double red[8];
+  __shared__ int flag;
+  const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+  const int sub = lane & (G - 1);
+  double nrm = 0.0;
+  const int64_t groups = (int64_t)gridDim.x * (blockDim.x / G);
+  const int64_t g0 = (int64_t)blockIdx.x * (blockDim.x / G) + t / G;
+  // every lane of a warp runs the same number of row iterations (rows past n are empty), so the
+  // shuffles below always see the whole warp
+  const int64_t rows_per_group = ((int64_t)n + groups - 1) / groups;
+  int p0 = 0, p1 = 0;
+  if (g0 < n) {
+    p0 = __ldg(row_ptr + g0);
+    p1 = __ldg(row_ptr + g0 + 1);
+  }
+  for (int64_t k = 0; k < rows_per_group; ++k) {
+    const int64_t i = g0 + k * groups;
+    const int64_t inext = i + groups;
+    int q0 = 0, q1 = 0;
+    if (inext < n) {
+      q0 = __ldg(row_ptr + inext);
+      q1 = __ldg(row_ptr + inext + 1);
+    }
+    double acc[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) acc[u] = 0.0;
+    for (int p = p0 + sub; p < p1; p += G * U) {
+      int c[U];
+      double v[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int q = p + u * G;
+        c[u] = q < p1 ? __ldg(col + q) : -1;
+        v[u] = q < p1 ? __ldg(vals + q) : 0.0;
+      }
+      double xv[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) xv[u] = c[u] >= 0 ? __ldg(x + c[u]) : 0.0;
+#pragma unroll
+      for (int u = 0; u < U; ++u) acc[u] = fma(v[u], xv[u], acc[u]);
+    }
+    double s = acc[0];
+#pragma unroll
+    for (int u = 1; u < U; ++u) s += acc[u];
+#pragma unroll
+    for (int o = G / 2; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (i < n && sub == 0) {
+      if (bsub) s = bsub[i] - s;
+      y[i] = s;
+      nrm = fma(s, s, nrm);
+    }
+    p0 = q0;
+    p1 = q1;
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) nrm += __shfl_xor_sync(0xffffffffu, nrm, o);
@@ -111,12 +197,29 @@ int grid_rows(int64_t n, int per_sm) {
 }
 }  // namespace
 
-int launch_spmv(int n, const int32_t* row_ptr, const int32_t* col, const double* vals, const double* x, double* y,
-                const double* bsub, double* partials, unsigned int* counter, int* err, const NormEpilogue& epi,
-                const Gate& gate, cudaStream_t stream) {
+// Lanes per row from the mean row length: one thread per row below 12 nonzeros per row
+// (stencils); 8 lanes (4 loads each in flight) below 48; 16 lanes above.
+int spmv_lanes_per_row(int n, int64_t nnz) {
+  const double mean = n > 0 ? static_cast<double>(nnz) / n : 0.0;
+  if (mean < 12.0) return 1;
+  return mean < 48.0 ? 8 : 16;
+}
+
+int launch_spmv(int n, int64_t nnz, const int32_t* row_ptr, const int32_t* col, const double* vals, const double* x,
+                double* y, const double* bsub, double* partials, unsigned int* counter, int* err,
+                const NormEpilogue& epi, const Gate& gate, cudaStream_t stream) {
   if (n <= 0) return CBG_OK;
-  const int grid = grid_rows(n, 8);
-  k_spmv<<<grid, 256, 0, stream>>>(n, row_ptr, col, vals, x, y, bsub, partials, counter, err, epi, gate);
+  const int g = spmv_lanes_per_row(n, nnz);
+  if (g == 1) {
+    const int grid = grid_rows(n, 8);
+    k_spmv<<<grid, 256, 0, stream>>>(n, row_ptr, col, vals, x, y, bsub, partials, counter, err, epi, gate);
+  } else {
+    const int grid = grid_rows((int64_t)n * g, 8);
+    if (g == 8)
+      k_spmv_vec<8, 4><<<grid, 256, 0, stream>>>(n, row_ptr, col, vals, x, y, bsub, partials, counter, err, epi, gate);
+    else
+      k_spmv_vec<16, 4><<<grid, 256, 0, stream>>>(n, row_ptr, col, vals, x, y, bsub, partials, counter, err, epi, gate);
+  }
   cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? CBG_OK : cuda_fail(e, "spmv launch");
 }

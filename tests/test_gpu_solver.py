@@ -18,12 +18,18 @@ def c1():
     return A, xt
 
 
-@pytest.mark.parametrize("matrix", ["c1", "3d", "powerlaw"])
+@pytest.mark.parametrize("matrix", ["c1", "3d", "powerlaw", "powerlaw_short", "powerlaw_long"])
 def test_spmv(cbg, orc, matrix):
+    # c1 and 3d take the thread-per-row kernel; the power-law matrices (mean row length ~15, ~29
+    # and ~58) take the lanes-per-row kernel with 8, 8 and 16 lanes
     if matrix == "c1":
         A, _ = c1()
     elif matrix == "3d":
         A = workloads.convdiff(20, 3, (1.0, 1.0, 1.0), 50.0)
+    elif matrix == "powerlaw_short":
+        A = workloads.powerlaw(20000, seed=3, mean_scale=5.0)
+    elif matrix == "powerlaw_long":
+        A = workloads.powerlaw(20000, seed=4, mean_scale=20.0)
     else:
         A = workloads.powerlaw(20000, seed=2)
     rp, col, vals = A.numpy()
@@ -156,3 +162,20 @@ def test_zero_rhs_and_max_iters(cbg, orc):
     assert not r.converged and r.status == -5 and r.iters == 25
     ref = orc.gmres(rp, col, vals, b.cpu().numpy(), restart=20, tol=1e-10, fmt=orc.FRSZ2, max_iters=25)
     assert abs(r.true_rrn - ref.true_rrn) <= 1e-6 * ref.true_rrn
+
+
+def test_gmres_powerlaw_parity(cbg, orc):
+    """A power-law random matrix (the long-row SpMV path) against the oracle's solve."""
+    A = workloads.powerlaw(3000, seed=2)
+    rp, col, vals = A.numpy()
+    b = orc.spmv(rp, col, vals, np.ones(A.n))
+    ref = orc.gmres(rp, col, vals, b, restart=30, tol=1e-10, fmt=orc.FRSZ2, l=32)
+    Ad = A.to("cuda")
+    S = cbg.Solver(Ad.row_ptr, Ad.col, Ad.vals, restart=30, tol=1e-10, fmt="frsz2", frsz2_bits=32)
+    x = torch.zeros(A.n, dtype=torch.float64, device="cuda")
+    r = S.solve(torch.from_numpy(b).cuda(), x)
+    S.close()
+    assert r.converged and r.true_rrn <= 1e-10
+    assert abs(r.iters - ref.iters) <= max(1, 0.02 * ref.iters)
+    xo = ref.x
+    assert np.linalg.norm(x.cpu().numpy() - xo) / np.linalg.norm(xo) <= 1e-8
