@@ -125,6 +125,10 @@ __global__ void __launch_bounds__(CastCfg::kThreads) k_dot_cast(BasisView B, int
   const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
   int64_t k0, k1;
   cta_value_range(B.n, gridDim.x, blockIdx.x, &k0, &k1);
+  // this CTA's vectors [v_lo, v_hi) (gridDim.y > 1 only when the values leave the GPU underfilled)
+  const int v_lo = static_cast<int>((int64_t)nvec * blockIdx.y / gridDim.y);
+  const int v_hi = static_cast<int>((int64_t)nvec * (blockIdx.y + 1) / gridDim.y);
+  const int cid = blockIdx.y * gridDim.x + blockIdx.x, nctas = gridDim.x * gridDim.y;
   for (int v = t; v < nvec; v += T) hpart[v] = 0.0;
   __syncthreads();
   int batch = 0;
@@ -135,24 +139,25 @@ __global__ void __launch_bounds__(CastCfg::kThreads) k_dot_cast(BasisView B, int
 #pragma unroll
     for (int i = 0; i < P; ++i) wv[i] = (active && kk + i < B.n) ? w[kk + i] : 0.0;
     double nxt[P];
-    if (active) load8_widen<F>(B.vals, kk, nxt);
-    for (int vec = 0; vec < nvec; ++vec) {
+    if (active && v_lo < v_hi) load8_widen<F>(B.vals + (int64_t)v_lo * B.vstride, kk, nxt);
+    for (int vec = v_lo; vec < v_hi; ++vec) {
       double cur[P];
 #pragma unroll
       for (int i = 0; i < P; ++i) cur[i] = nxt[i];
-      if (active && vec + 1 < nvec) load8_widen<F>(B.vals + (int64_t)(vec + 1) * B.vstride, kk, nxt);
+      if (active && vec + 1 < v_hi) load8_widen<F>(B.vals + (int64_t)(vec + 1) * B.vstride, kk, nxt);
       double hp = 0.0;
       if (active) {
 #pragma unroll
         for (int i = 0; i < P; ++i)
           if (kk + i < B.n) hp = fma(cur[i], wv[i], hp);  // the padding past n may hold anything
       }
-      red[((batch & 1) * R + (vec % R)) * T + t] = hp;
+      const int vi = vec - v_lo;
+      red[((batch & 1) * R + (vi % R)) * T + t] = hp;
       __syncthreads();
-      if (vec % R == R - 1 || vec == nvec - 1) {
-        const int first = vec - (vec % R);
+      if (vi % R == R - 1 || vec == v_hi - 1) {
+        const int first = vec - (vi % R);
         for (int vv = first + warp; vv <= vec; vv += T / 32) {
-          const double* r = red + ((batch & 1) * R + (vv % R)) * T;
+          const double* r = red + ((batch & 1) * R + ((vv - v_lo) % R)) * T;
           double s = 0.0;
           for (int i = lane; i < T; i += 32) s += r[i];
 #pragma unroll
@@ -164,10 +169,10 @@ __global__ void __launch_bounds__(CastCfg::kThreads) k_dot_cast(BasisView B, int
     }
   }
   __syncthreads();
-  for (int v = t; v < nvec; v += T) partials[(size_t)blockIdx.x * nvec + v] = hpart[v];
-  if (arrive_last(counter, gridDim.x, &flags[0])) {
+  for (int v = t; v < nvec; v += T) partials[(size_t)cid * nvec + v] = hpart[v];
+  if (arrive_last(counter, nctas, &flags[0])) {
     for (int v = warp; v < nvec; v += T / 32) {
-      const double sum = warp_sum_strided(partials + v, gridDim.x, nvec);
+      const double sum = warp_sum_strided(partials + v, nctas, nvec);
       if (lane == 0) out[v] = sum;
     }
     if (t == 0) *counter = 0;
@@ -274,7 +279,7 @@ std::unordered_map<FnKey, size_t, FnKeyHash> g_smem_limit;  // dynamic smem limi
 }  // namespace
 
 int basis_launch_config(const void* fn, int threads, size_t smem, int64_t units, int64_t units_per_cta_min,
-                        int max_grid, int* grid) {
+                        int max_grid, int* grid, int* full) {
   DeviceInfo di;
   int st = device_info(&di);
   if (st) return st;
@@ -305,6 +310,7 @@ int basis_launch_config(const void* fn, int threads, size_t smem, int64_t units,
     }
   }
   int64_t g = (int64_t)occ * di.sms;
+  if (full) *full = static_cast<int>(g);
   int64_t need = (units + units_per_cta_min - 1) / units_per_cta_min;
   if (need < 1) need = 1;
   if (g > need) g = need;
@@ -327,9 +333,10 @@ int cast_dot_launch(const BasisView& B, int nvec, const double* w, double* out, 
     default: return CBG_ERR_INVALID_ARG;
   }
   const size_t smem = CastCfg::dot_smem(nvec);
-  int grid;
-  int st = basis_launch_config(fn, CastCfg::kThreads, smem, B.n, 4096, max_grid, &grid);
+  int gx, full;
+  int st = basis_launch_config(fn, CastCfg::kThreads, smem, B.n, 4096, max_grid, &gx, &full);
   if (st) return st;
+  const dim3 grid(gx, dot_vector_split(gx, full, nvec, max_grid));
   const int T = CastCfg::kThreads;
   switch (B.fmt) {
     case CBG_FP64: k_dot_cast<CBG_FP64><<<grid, T, smem, stream>>>(B, nvec, w, out, partials, counter, gate); break;
@@ -342,6 +349,16 @@ int cast_dot_launch(const BasisView& B, int nvec, const double* w, double* out, 
 }
 
 }  // namespace
+
+// Vector slices for a dot whose block grid gx leaves the GPU (full resident CTAs) underfilled: up to
+// full / gx slices, at least one vector each, and gx * slices <= max_grid.
+int dot_vector_split(int gx, int full, int nvec, int max_grid) {
+  int64_t ny = gx > 0 ? full / gx : 1;
+  if (ny > nvec) ny = nvec;
+  const int64_t cap = (max_grid < kMaxGrid ? max_grid : kMaxGrid) / (gx > 0 ? gx : 1);
+  if (ny > cap) ny = cap;
+  return ny < 1 ? 1 : static_cast<int>(ny);
+}
 
 int launch_basis_dot(const BasisView& B, int nvec, const double* w, double* out, double* partials, unsigned int* counter,
                      int* err, const Gate& gate, cudaStream_t stream) {
@@ -376,7 +393,7 @@ int launch_basis_update(const BasisView& B, int nvec, const int* nvec_dev, const
   }
   const size_t smem = (size_t)nvec * 8 + (CastCfg::kThreads / 32) * 8 + 16;
   int grid;
-  int st = basis_launch_config(fn, CastCfg::kThreads, smem, B.n, 2048, kMaxGrid, &grid);
+  int st = basis_launch_config(fn, CastCfg::kThreads, smem, B.n, 2048, kMaxGrid, &grid, nullptr);
   if (st) return st;
   const int T = CastCfg::kThreads;
   switch (B.fmt) {

@@ -27,7 +27,8 @@
 namespace cbg {
 
 // ================================================================================================
-// dot: one thread per 32-value block, 128 blocks per tile, every vector of the basis per tile
+// dot: one thread per 32-value block, 128 blocks per tile; CTA (x, y) takes block range x and the
+// y-th slice of the vectors (gridDim.y > 1 only when the blocks alone leave the GPU underfilled)
 // ================================================================================================
 
 template <int L>
@@ -140,7 +141,11 @@ __global__ void __launch_bounds__(FDot<L>::kThreads) k_dot_frsz2(BasisView B, in
   int64_t b0, b1;
   cta_block_range(nb, gridDim.x, blockIdx.x, &b0, &b1);
   const int ntiles = static_cast<int>((b1 - b0 + T - 1) / T);
-  const int total = ntiles * nvec;
+  // this CTA's vectors [v_lo, v_lo + nv)
+  const int v_lo = static_cast<int>((int64_t)nvec * blockIdx.y / gridDim.y);
+  const int nv = static_cast<int>((int64_t)nvec * (blockIdx.y + 1) / gridDim.y) - v_lo;
+  const int total = ntiles * nv;
+  const int cid = blockIdx.y * gridDim.x + blockIdx.x, nctas = gridDim.x * gridDim.y;
 
   for (int i = t; i < C::kWarps * nvec; i += T) hpart[i] = 0.0;
   if (t == 0) {
@@ -154,7 +159,7 @@ __global__ void __launch_bounds__(FDot<L>::kThreads) k_dot_frsz2(BasisView B, in
   __syncthreads();
 
   auto issue = [&](int p) {
-    const int tile = p / nvec, vec = p - tile * nvec, s = p % S;
+    const int tile = p / nv, vec = v_lo + (p - tile * nv), s = p % S;
     const int64_t tb0 = b0 + (int64_t)tile * T;
     const int nbt = static_cast<int>(min((int64_t)T, b1 - tb0));
     const uint32_t cbytes = static_cast<uint32_t>((nbt * L * 4 + 15) & ~15);
@@ -221,7 +226,7 @@ __global__ void __launch_bounds__(FDot<L>::kThreads) k_dot_frsz2(BasisView B, in
 #pragma unroll
       for (int r = 0; r < 32; ++r) W1[r] = W0[r] = 0;
     }
-    for (int vec = 0; vec < nvec; ++vec) {
+    for (int vi = 0; vi < nv; ++vi) {
       // lagged refill: the stage released by every warp in the previous iteration
       if (t == 0 && !first && issued < total && !rfail && !dead) {
         if (mbar_wait_bounded(&empty[ps], pph)) {
@@ -257,7 +262,7 @@ __global__ void __launch_bounds__(FDot<L>::kThreads) k_dot_frsz2(BasisView B, in
         const int x = (e > 1 ? static_cast<int>(e) : 1) + ew - 2096 - L;
         hp = scale_pow2(static_cast<double>(th), x + L - 5);
       }
-      myred[(vec % C::kBatch) * C::kRedStride + lane] = hp;
+      myred[(vi % C::kBatch) * C::kRedStride + lane] = hp;
       __syncwarp();
       if (lane == 0 && ok) mbar_arrive(&empty[s]);
       ps = s;
@@ -267,8 +272,8 @@ __global__ void __launch_bounds__(FDot<L>::kThreads) k_dot_frsz2(BasisView B, in
         s = 0;
         ph ^= 1u;
       }
-      if (vec % C::kBatch == C::kBatch - 1 || vec == nvec - 1) {
-        const int first_v = vec - (vec % C::kBatch), cnt = vec - first_v + 1;
+      if (vi % C::kBatch == C::kBatch - 1 || vi == nv - 1) {
+        const int first_i = vi - (vi % C::kBatch), cnt = vi - first_i + 1, first_v = v_lo + first_i;
         const int v = lane & 7, part = lane >> 3;
         double sacc = 0.0;
         if (v < cnt) {
@@ -291,15 +296,17 @@ __global__ void __launch_bounds__(FDot<L>::kThreads) k_dot_frsz2(BasisView B, in
     }
     return;
   }
+  // every CTA writes all nvec partials (zero outside its vectors), so the final sums run over the
+  // same CTAs in the same order for every vector
   for (int v = t; v < nvec; v += T) {
     double sacc = 0.0;
 #pragma unroll
     for (int i = 0; i < C::kWarps; ++i) sacc += hpart[i * nvec + v];
-    partials[(size_t)blockIdx.x * nvec + v] = sacc;
+    partials[(size_t)cid * nvec + v] = sacc;
   }
-  if (arrive_last(counter, gridDim.x, &flags[1])) {
+  if (arrive_last(counter, nctas, &flags[1])) {
     for (int v = warp; v < nvec; v += C::kWarps) {
-      const double sum = warp_sum_strided(partials + v, gridDim.x, nvec);
+      const double sum = warp_sum_strided(partials + v, nctas, nvec);
       if (lane == 0) out[v] = sum;
     }
     if (t == 0) *counter = 0;
@@ -705,9 +712,10 @@ int frsz2_dot_launch(const BasisView& B, int nvec, const double* w, double* out,
     case 16: fn = fnp(k_dot_frsz2<16>); smem = FDot<16>::smem_bytes(nvec); break;
     default: return CBG_ERR_INVALID_ARG;
   }
-  int grid;
-  int st = basis_launch_config(fn, 128, smem, (B.n + 31) / 32, 16, max_grid, &grid);
+  int gx, full;
+  int st = basis_launch_config(fn, 128, smem, (B.n + 31) / 32, 16, max_grid, &gx, &full);
   if (st) return st;
+  const dim3 grid(gx, dot_vector_split(gx, full, nvec, max_grid));
   switch (B.l) {
     case 32: k_dot_frsz2<32><<<grid, 128, smem, stream>>>(B, nvec, w, out, partials, counter, err, gate); break;
     case 21: k_dot_frsz2<21><<<grid, 128, smem, stream>>>(B, nvec, w, out, partials, counter, err, gate); break;
@@ -729,7 +737,7 @@ int frsz2_update_launch(const BasisView& B, int nvec, const int* nvec_dev, const
     default: return CBG_ERR_INVALID_ARG;
   }
   int grid;
-  int st = basis_launch_config(fn, 128, smem, (B.n + 31) / 32, 8, kMaxGrid, &grid);
+  int st = basis_launch_config(fn, 128, smem, (B.n + 31) / 32, 8, kMaxGrid, &grid, nullptr);
   if (st) return st;
   switch (B.l) {
     case 32: k_update_frsz2<32><<<grid, 128, smem, stream>>>(B, nvec, nvec_dev, h, negate, w, partials, counter, err, epi, gate); break;

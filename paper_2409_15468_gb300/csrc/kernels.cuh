@@ -55,9 +55,11 @@ __device__ __forceinline__ void norm_epilogue(const NormEpilogue& e, double norm
 
 // ---- basis.cu / basis_frsz2.cu -----------------------------------------------------------------
 // Grid for a reducing basis kernel: occupancy x SMs, at most one CTA per units_per_cta_min units,
-// at most max_grid (and kMaxGrid). Raises the kernel's dynamic shared memory limit once.
+// at most max_grid (and kMaxGrid); *full (if not null) receives occupancy x SMs. Raises the
+// kernel's dynamic shared memory limit once.
 int basis_launch_config(const void* fn, int threads, size_t smem, int64_t units, int64_t units_per_cta_min,
-                        int max_grid, int* grid);
+                        int max_grid, int* grid, int* full);
+int dot_vector_split(int gx, int full, int nvec, int max_grid);
 int frsz2_dot_launch(const BasisView& B, int nvec, const double* w, double* out, double* partials,
                      unsigned int* counter, int* err, const Gate& gate, int max_grid, cudaStream_t stream);
 int frsz2_update_launch(const BasisView& B, int nvec, const int* nvec_dev, const double* h, int negate, double* w,

@@ -53,79 +53,135 @@ __global__ void k_set_bnorm(SolverCtl* ctl, const double* bnorm2, double tol, do
 // Column j of the least-squares problem (step 17, one column at a time): finish h with the second
 // pass (step 9), set h_{j+1,j} (steps 6/10), test for breakdown (step 12), apply the previous
 // Givens rotations, form the new one and rotate beta e1. |g_{j+1}| / ||b|| is the implicit residual.
-__global__ void k_givens(GivensArgs a, int j) {
-  if (threadIdx.x != 0) return;
+// One warp stages the column and the previous rotations in shared memory; lane 0 then runs the
+// sequential recurrence on shared memory (no dependent global loads in the loop).
+constexpr int kMaxRestart = 1024;
+__global__ void __launch_bounds__(32) k_givens(GivensArgs a, int j) {
+  __shared__ double col[kMaxRestart + 2];
+  __shared__ double scs[kMaxRestart], ssn[kMaxRestart];
   SolverCtl* c = a.ctl;
-  if (c->stop) return;
+  if (*(volatile const int*)&c->stop) return;  // every lane reads it before lane 0 may write it
+  const int lane = threadIdx.x;
   const int ld = a.m + 1;
   double* hcol = a.H + (size_t)j * ld;
   const int reorth = c->reorth;
-  if (reorth) {
-    for (int i = 0; i <= j; ++i) hcol[i] += a.u[i];
-    c->reorth_count += 1;
+  for (int i = lane; i <= j; i += 32) {
+    double h = hcol[i];
+    if (reorth) {
+      h += a.u[i];
+      hcol[i] = h;
+    }
+    col[i] = h;
   }
-  const double hn = sqrt(c->hn2);
-  hcol[j + 1] = hn;
-  const bool breakdown = (hn == 0.0) || (reorth && hn < c->eta * sqrt(c->hn2_first));
+  for (int i = lane; i < j; i += 32) {
+    scs[i] = a.cs[i];
+    ssn[i] = a.sn[i];
+  }
+  __syncwarp();
+  if (lane == 0) {
+    if (reorth) c->reorth_count += 1;
+    const double hn = sqrt(c->hn2);
+    hcol[j + 1] = hn;
+    col[j + 1] = hn;
+    const bool breakdown = (hn == 0.0) || (reorth && hn < c->eta * sqrt(c->hn2_first));
+    for (int i = 0; i < j; ++i) {
+      const double t = scs[i] * col[i] + ssn[i] * col[i + 1];
+      col[i + 1] = -ssn[i] * col[i] + scs[i] * col[i + 1];
+      col[i] = t;
+    }
+    const double x = col[j], y = col[j + 1];
+    double cs, sn;
+    if (y == 0.0) {
+      cs = 1.0;
+      sn = 0.0;
+    } else {
+      const double r = hypot(x, y);
+      cs = x / r;
+      sn = y / r;
+      col[j] = r;
+    }
+    col[j + 1] = 0.0;
+    a.cs[j] = cs;
+    a.sn[j] = sn;
+    a.g[j + 1] = -sn * a.g[j];
+    a.g[j] = cs * a.g[j];
+    const double implicit = fabs(a.g[j + 1]) / c->bnorm;
+    c->implicit = implicit;
+    if (a.hist && a.hist_off + j < a.hist_cap) a.hist[a.hist_off + j] = implicit;
+    c->m_eff = j + 1;
+    if (breakdown) c->breakdown = 1;
+    if (!isfinite(implicit)) {
+      c->err |= kDevErrNonFinite;
+      c->stop = 1;
+    }
+    if (breakdown || implicit <= c->tol || j + 1 >= c->steps_allowed) c->stop = 1;
+    c->rcp = hn > 0.0 ? 1.0 / hn : 0.0;
+    c->reorth = 0;
+  }
+  __syncwarp();
   double* Rj = a.R + (size_t)j * ld;
-  for (int i = 0; i <= j + 1; ++i) Rj[i] = hcol[i];
-  for (int i = 0; i < j; ++i) {
-    const double t = a.cs[i] * Rj[i] + a.sn[i] * Rj[i + 1];
-    Rj[i + 1] = -a.sn[i] * Rj[i] + a.cs[i] * Rj[i + 1];
-    Rj[i] = t;
-  }
-  const double x = Rj[j], y = Rj[j + 1];
-  double cs, sn;
-  if (y == 0.0) {
-    cs = 1.0;
-    sn = 0.0;
-  } else {
-    const double r = hypot(x, y);
-    cs = x / r;
-    sn = y / r;
-    Rj[j] = r;
-  }
-  Rj[j + 1] = 0.0;
-  a.cs[j] = cs;
-  a.sn[j] = sn;
-  a.g[j + 1] = -sn * a.g[j];
-  a.g[j] = cs * a.g[j];
-  const double implicit = fabs(a.g[j + 1]) / c->bnorm;
-  c->implicit = implicit;
-  if (a.hist && a.hist_off + j < a.hist_cap) a.hist[a.hist_off + j] = implicit;
-  c->m_eff = j + 1;
-  if (breakdown) c->breakdown = 1;
-  if (!isfinite(implicit)) {
-    c->err |= kDevErrNonFinite;
-    c->stop = 1;
-  }
-  if (breakdown || implicit <= c->tol || j + 1 >= c->steps_allowed) c->stop = 1;
-  c->rcp = hn > 0.0 ? 1.0 / hn : 0.0;
-  c->reorth = 0;
+  for (int i = lane; i <= j + 1; i += 32) Rj[i] = col[i];
 }
 
-// y := R^{-1} g over the leading columns with a nonzero diagonal (step 17), one warp.
-__global__ void k_backsub(GivensArgs a, double* y) {
+// y := R^{-1} g over the leading columns with a nonzero diagonal (step 17). The CTA finds the first
+// zero pivot in parallel and, for restarts up to kBacksubStaged, stages the upper triangle of R
+// transposed in shared memory (rows contiguous); one warp then runs the substitution.
+constexpr int kBacksubStaged = 128;
+__global__ void __launch_bounds__(256) k_backsub(GivensArgs a, double* y) {
+  extern __shared__ double sT[];  // [mls][mls] rows of R, then y[mls] (staged case only)
+  __shared__ int s_mls;
   SolverCtl* c = a.ctl;
-  const int lane = threadIdx.x;
+  const int t = threadIdx.x, lane = t & 31;
   const int ld = a.m + 1;
   const int m_eff = c->m_eff;
-  int mls = m_eff;
-  for (int k = 0; k < m_eff; ++k) {
-    if (a.R[(size_t)k * ld + k] == 0.0) {
-      mls = k;
-      break;
+  if (t == 0) s_mls = m_eff;
+  __syncthreads();
+  for (int k = t; k < m_eff; k += blockDim.x)
+    if (a.R[(size_t)k * ld + k] == 0.0) atomicMin(&s_mls, k);
+  __syncthreads();
+  const int mls = s_mls;
+  const bool staged = a.m <= kBacksubStaged;
+  if (staged) {
+    for (int idx = t; idx < mls * mls; idx += blockDim.x) {
+      const int cl = idx / mls, r = idx - cl * mls;  // consecutive threads read down a column
+      if (r <= cl) sT[r * mls + cl] = a.R[(size_t)cl * ld + r];
     }
+    __syncthreads();
   }
+  if (t >= 32) return;
+  double* sy = sT + mls * mls;
   for (int k = mls - 1; k >= 0; --k) {
     double s = 0.0;
-    for (int i = k + 1 + lane; i < mls; i += 32) s += a.R[(size_t)i * ld + k] * y[i];
+    if (staged) {
+      for (int i = k + 1 + lane; i < mls; i += 32) s += sT[k * mls + i] * sy[i];
+    } else {
+      for (int i = k + 1 + lane; i < mls; i += 32) s += a.R[(size_t)i * ld + k] * y[i];
+    }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-    if (lane == 0) y[k] = (a.g[k] - s) / a.R[(size_t)k * ld + k];
+    if (lane == 0) {
+      const double yk = (a.g[k] - s) / (staged ? sT[k * mls + k] : a.R[(size_t)k * ld + k]);
+      y[k] = yk;
+      if (staged) sy[k] = yk;
+    }
     __syncwarp();
   }
   if (lane == 0) c->m_ls = mls;
+}
+
+int launch_backsub(const GivensArgs& a, double* y, cudaStream_t stream) {
+  size_t smem = 0;
+  if (a.m <= kBacksubStaged) {
+    smem = (size_t)(a.m * a.m + a.m) * sizeof(double);
+    if (smem > 48 * 1024) {
+      cudaError_t e = cudaFuncSetAttribute(k_backsub, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           static_cast<int>(smem));
+      if (e != cudaSuccess) return cuda_fail(e, "back substitution smem attribute");
+    }
+  }
+  k_backsub<<<1, 256, smem, stream>>>(a, y);
+  cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? CBG_OK : cuda_fail(e, "back substitution launch");
 }
 
 int launch_givens(const GivensArgs& a, int j, cudaStream_t stream) {
@@ -322,11 +378,10 @@ int enqueue_restart(cbg_ctx* c) {
   const BasisView B = view_of(c);
   SolverCtl* ctl = c->ctl;
   GivensArgs a = givens_args(c);
-  k_backsub<<<1, 32, 0, c->stream>>>(a, c->y);
-  cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess) return cuda_fail(e, "back substitution launch");
+  int st = launch_backsub(a, c->y, c->stream);
+  if (st) return st;
   NormEpilogue none{nullptr, nullptr, kEpiNone};
-  int st = launch_basis_update(B, c->opts.restart, &ctl->m_ls, c->y, 1, c->x, c->partials, &ctl->counters[kCtrUpdate],
+  st = launch_basis_update(B, c->opts.restart, &ctl->m_ls, c->y, 1, c->x, c->partials, &ctl->counters[kCtrUpdate],
                                &ctl->err, none, Gate{nullptr, nullptr}, c->stream);
   if (st) return st;
   return enqueue_residual(c);
