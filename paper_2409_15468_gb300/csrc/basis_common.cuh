@@ -15,6 +15,15 @@ __device__ __forceinline__ void cta_block_range(int64_t nb, int G, int c, int64_
   *b1 = u1 * 4 < nb ? u1 * 4 : nb;
 }
 
+// Slice y of `slices` holds vectors [floor(nvec y / slices), floor(nvec (y + 1) / slices)); the
+// slice of vector v.
+__device__ __forceinline__ int vector_slice(int v, int nvec, int slices) {
+  int y = static_cast<int>(((int64_t)(v + 1) * slices - 1) / nvec);
+  while (y + 1 < slices && (int64_t)nvec * (y + 1) / slices <= v) ++y;
+  while (y > 0 && (int64_t)nvec * y / slices > v) --y;
+  return y;
+}
+
 __device__ __forceinline__ bool gate_skip(const Gate& g) {
   if (g.stop && *(volatile const int*)g.stop) return true;
   if (g.need && !*(volatile const int*)g.need) return true;

@@ -296,9 +296,9 @@ __global__ void __launch_bounds__(FDot<L>::kThreads) k_dot_frsz2(BasisView B, in
     }
     return;
   }
-  // every CTA writes all nvec partials (zero outside its vectors), so the final sums run over the
-  // same CTAs in the same order for every vector
-  for (int v = t; v < nvec; v += T) {
+  // partials of this CTA's vectors; vector v is then summed over the gridDim.x CTAs of its slice,
+  // in a fixed order
+  for (int v = v_lo + t; v < v_lo + nv; v += T) {
     double sacc = 0.0;
 #pragma unroll
     for (int i = 0; i < C::kWarps; ++i) sacc += hpart[i * nvec + v];
@@ -306,7 +306,8 @@ __global__ void __launch_bounds__(FDot<L>::kThreads) k_dot_frsz2(BasisView B, in
   }
   if (arrive_last(counter, nctas, &flags[1])) {
     for (int v = warp; v < nvec; v += C::kWarps) {
-      const double sum = warp_sum_strided(partials + v, nctas, nvec);
+      const int y = vector_slice(v, nvec, gridDim.y);
+      const double sum = warp_sum_strided(partials + (size_t)y * gridDim.x * nvec + v, gridDim.x, nvec);
       if (lane == 0) out[v] = sum;
     }
     if (t == 0) *counter = 0;
@@ -318,17 +319,19 @@ __global__ void __launch_bounds__(FDot<L>::kThreads) k_dot_frsz2(BasisView B, in
 // per pipeline stage, vectors in groups of at most 32 (the exact integer sums are per group)
 // ================================================================================================
 
-template <int L>
+// S pipeline stages: 3 when the grid fills the GPU (occupancy matters); 12 when it does not (small
+// n: each CTA then has little work per stage, and only more copies in flight hide the latency).
+template <int L, int S = 3>
 struct FUpd {
   static constexpr int kThreads = 128;
   static constexpr int kWarps = 4;
   static constexpr int kBlocks = 32;
   static constexpr int kVps = 2;  // basis vectors per stage
-  static constexpr int kStages = 3;
+  static constexpr int kStages = S;
   static constexpr int kGroup = 32;
   // resident CTAs per SM the register allocation is capped for (l < 32 is faster with a few spills
-  // and one more CTA)
-  static constexpr int kMinBlocks = L == 32 ? 5 : 6;
+  // and one more CTA); the deep pipeline runs one CTA per SM
+  static constexpr int kMinBlocks = S != 3 ? 1 : (L == 32 ? 5 : 6);
   static constexpr int kVecBytes = kBlocks * L * 4;
   static constexpr int kStageBytes = kVps * kVecBytes;
   // dynamic smem: stages | coefficient table [kGroup][kBlocks] (int2) | exponent words of one group
@@ -375,14 +378,14 @@ __device__ __forceinline__ void load_codes8(const uint32_t* st, int t, uint32_t 
   }
 }
 
-template <int L>
-__global__ void __launch_bounds__(FUpd<L>::kThreads, FUpd<L>::kMinBlocks) k_update_frsz2(BasisView B, int nvec_arg, const int* nvec_dev,
+template <int L, int SD>
+__global__ void __launch_bounds__(FUpd<L, SD>::kThreads, FUpd<L, SD>::kMinBlocks) k_update_frsz2(BasisView B, int nvec_arg, const int* nvec_dev,
                                                                     const double* __restrict__ hcoef, int negate,
                                                                     double* __restrict__ w,
                                                                     double* __restrict__ partials,
                                                                     unsigned int* counter, int* err, NormEpilogue epi,
                                                                     Gate gate) {
-  using C = FUpd<L>;
+  using C = FUpd<L, SD>;
   constexpr int T = C::kThreads, NBT = C::kBlocks, G = C::kGroup, S = C::kStages, VPS = C::kVps;
   if (gate_skip(gate)) return;
   const int nvec = nvec_dev ? *(volatile const int*)nvec_dev : nvec_arg;
@@ -725,27 +728,48 @@ int frsz2_dot_launch(const BasisView& B, int nvec, const double* w, double* out,
   return e == cudaSuccess ? CBG_OK : cuda_fail(e, "frsz2 dot launch");
 }
 
+namespace {
+
+template <int L, int S>
+int frsz2_update_launch_t(const BasisView& B, int nvec, const int* nvec_dev, const double* h, int negate, double* w,
+                          double* partials, unsigned int* counter, int* err, const NormEpilogue& epi,
+                          const Gate& gate, int grid, cudaStream_t stream) {
+  const void* fn = fnp(k_update_frsz2<L, S>);
+  const size_t smem = FUpd<L, S>::smem_bytes(nvec);
+  int g;
+  int st = basis_launch_config(fn, 128, smem, (B.n + 31) / 32, 8, kMaxGrid, &g, nullptr);
+  if (st) return st;
+  if (grid > 0 && grid < g) g = grid;
+  k_update_frsz2<L, S><<<g, 128, smem, stream>>>(B, nvec, nvec_dev, h, negate, w, partials, counter, err, epi, gate);
+  cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? CBG_OK : cuda_fail(e, "frsz2 update launch");
+}
+
+template <int L>
+int frsz2_update_launch_l(const BasisView& B, int nvec, const int* nvec_dev, const double* h, int negate, double* w,
+                          double* partials, unsigned int* counter, int* err, const NormEpilogue& epi,
+                          const Gate& gate, cudaStream_t stream) {
+  DeviceInfo di;
+  int st = device_info(&di);
+  if (st) return st;
+  // CTAs the blocks need (8 blocks at least per CTA): fewer than SMs means an underfilled GPU
+  const int64_t need = ((B.n + 31) / 32 + 7) / 8;
+  if (need < di.sms)
+    return frsz2_update_launch_t<L, 12>(B, nvec, nvec_dev, h, negate, w, partials, counter, err, epi, gate, 0, stream);
+  return frsz2_update_launch_t<L, 3>(B, nvec, nvec_dev, h, negate, w, partials, counter, err, epi, gate, 0, stream);
+}
+
+}  // namespace
+
 int frsz2_update_launch(const BasisView& B, int nvec, const int* nvec_dev, const double* h, int negate, double* w,
                         double* partials, unsigned int* counter, int* err, const NormEpilogue& epi,
                         const Gate& gate, cudaStream_t stream) {
-  const void* fn;
-  size_t smem;
   switch (B.l) {
-    case 32: fn = fnp(k_update_frsz2<32>); smem = FUpd<32>::smem_bytes(nvec); break;
-    case 21: fn = fnp(k_update_frsz2<21>); smem = FUpd<21>::smem_bytes(nvec); break;
-    case 16: fn = fnp(k_update_frsz2<16>); smem = FUpd<16>::smem_bytes(nvec); break;
+    case 32: return frsz2_update_launch_l<32>(B, nvec, nvec_dev, h, negate, w, partials, counter, err, epi, gate, stream);
+    case 21: return frsz2_update_launch_l<21>(B, nvec, nvec_dev, h, negate, w, partials, counter, err, epi, gate, stream);
+    case 16: return frsz2_update_launch_l<16>(B, nvec, nvec_dev, h, negate, w, partials, counter, err, epi, gate, stream);
     default: return CBG_ERR_INVALID_ARG;
   }
-  int grid;
-  int st = basis_launch_config(fn, 128, smem, (B.n + 31) / 32, 8, kMaxGrid, &grid, nullptr);
-  if (st) return st;
-  switch (B.l) {
-    case 32: k_update_frsz2<32><<<grid, 128, smem, stream>>>(B, nvec, nvec_dev, h, negate, w, partials, counter, err, epi, gate); break;
-    case 21: k_update_frsz2<21><<<grid, 128, smem, stream>>>(B, nvec, nvec_dev, h, negate, w, partials, counter, err, epi, gate); break;
-    default: k_update_frsz2<16><<<grid, 128, smem, stream>>>(B, nvec, nvec_dev, h, negate, w, partials, counter, err, epi, gate); break;
-  }
-  cudaError_t e = cudaGetLastError();
-  return e == cudaSuccess ? CBG_OK : cuda_fail(e, "frsz2 update launch");
 }
 
 }  // namespace cbg
