@@ -252,15 +252,22 @@ def time_to_tol(pkg, torch, device, repeats=3):
 
 
 def solve_c3(pkg, torch, device, formats, N: int = 256, restart: int = 100, tol: float = 1e-10,
-             max_iters: int = 20000, verify: bool = True):
-    """Full CB-GMRES(restart) solves on the 3D 7-point convection-diffusion system on an N^3 grid
-    (wind (1,1,1), Peclet 50, b = A 1, x0 = 0) to a relative residual of tol, one per basis
-    format, through cbgmres_solve with device-resident b and x. Each final x is checked on the
-    host with the oracle's SpMV and compensated dot: ||b - A x|| / ||b|| recomputed independently
-    of the GPU path."""
+             max_iters: int = 20000, verify: bool = True, matrix: str = "c3"):
+    """Full CB-GMRES(restart) solves to a relative residual of tol, one per basis format, through
+    cbgmres_solve with device-resident b = A 1 and x0 = 0, on
+      c3: the 3D 7-point convection-diffusion system on an N^3 grid (wind (1,1,1), Peclet 50);
+      c4: the 4M-row power-law random matrix (row lengths Pareto, mean ~30, max 2000; seed 2).
+    Each final x is checked on the host with the oracle's SpMV and compensated dot:
+    ||b - A x|| / ||b|| recomputed independently of the GPU path."""
     import workloads
 
-    A = workloads.convdiff(N, 3, (1.0, 1.0, 1.0), 50.0, device=device)
+    if matrix == "c4":
+        A = workloads.powerlaw(1 << 22, seed=2, device=device)
+        desc = (f"power-law random nonsymmetric n={A.n}, nnz={A.nnz} (row lengths min(2000, floor(10 U^-1/1.5))"
+                f", N(0,1) off-diagonals, diag 1.2 x row abs-sum, seed 2)")
+    else:
+        A = workloads.convdiff(N, 3, (1.0, 1.0, 1.0), 50.0, device=device)
+        desc = f"3D 7-point convection-diffusion {N}^3 (n={A.n}, nnz={A.nnz}), wind (1,1,1)*50"
     b = pkg.spmv(A.row_ptr, A.col, A.vals, torch.ones(A.n, dtype=torch.float64, device=device)).clone()
     host = None
     if verify:
@@ -270,8 +277,19 @@ def solve_c3(pkg, torch, device, formats, N: int = 256, restart: int = 100, tol:
         rp, col, vals = A.numpy()
         bh = b.cpu().numpy()
         host = (oracle, rp, col, vals, bh, oracle.nrm2(bh))
-    out = {"config": f"3D 7-point convection-diffusion {N}^3 (n={A.n}, nnz={A.nnz}), wind (1,1,1)*50, b = A*1, "
-                     f"x0 = 0, restart {restart}, tol {tol}, max_iters {max_iters}"}
+    out = {"config": f"{desc}, b = A*1, x0 = 0, restart {restart}, tol {tol}, max_iters {max_iters}"}
+    # SpMV alone (algorithmic bytes: values and column indices, row pointers, x once, y)
+    y = torch.empty_like(b)
+    for _ in range(3):
+        pkg.spmv(A.row_ptr, A.col, A.vals, b, y=y)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(10):
+        pkg.spmv(A.row_ptr, A.col, A.vals, b, y=y)
+    e1.record()
+    torch.cuda.synchronize()
+    sp_ms = e0.elapsed_time(e1) / 10
+    out["spmv"] = {"ms": sp_ms, "gbs": (12 * A.nnz + 4 * (A.n + 1) + 16 * A.n) / (sp_ms * 1e-3) / 1e9}
     for f in formats:
         fmt, bits = (f.split("_")[0], int(f.split("_")[1])) if f.startswith("frsz2") else (f, 32)
         S = pkg.Solver(A.row_ptr, A.col, A.vals, restart=restart, tol=tol, fmt=fmt, frsz2_bits=bits,
@@ -294,6 +312,90 @@ def solve_c3(pkg, torch, device, formats, N: int = 256, restart: int = 100, tol:
         torch.cuda.empty_cache()
     if "fp64" in out and "frsz2_32" in out:
         out["speedup_frsz2_32_vs_fp64"] = out["fp64"]["seconds"] / out["frsz2_32"]["seconds"]
+    return out
+
+
+ALL_FORMATS = ["fp64", "fp32", "fp16", "bf16", "frsz2_16", "frsz2_21", "frsz2_32"]
+
+
+def exponent_spread(v: np.ndarray) -> dict:
+    """Per 32-value block of a Krylov vector: the spread e_max - e_min of the IEEE exponents of its
+    nonzero values (the quantity FRSZ2 truncates against), as a histogram, and the fraction of
+    nonzero values each FRSZ2 width stores as zero (block-relative exponent gap >= l - 1)."""
+    n = v.size
+    nb = (n + 31) // 32
+    pad = np.zeros(nb * 32)
+    pad[:n] = v
+    e = ((pad.view(np.uint64) >> np.uint64(52)) & np.uint64(0x7FF)).astype(np.int64).reshape(nb, 32)
+    nz = e > 0
+    emax = e.max(axis=1)
+    emin = np.where(nz, e, 1 << 12).min(axis=1)
+    spread = np.where(nz.any(axis=1), emax - emin, 0)
+    hist = np.bincount(np.minimum(spread, 64), minlength=65)
+    gap = emax[:, None] - e
+    total = max(int(nz.sum()), 1)
+    return {"spread_hist": {str(i): int(c) for i, c in enumerate(hist) if c},
+            "spread_quantiles": {q: float(np.quantile(spread, float(q))) for q in ("0.5", "0.9", "0.99")},
+            "zero_fraction": {f"frsz2_{l}": float(((gap >= l - 1) & nz).sum() / total) for l in (16, 21, 32)}}
+
+
+def sweep(pkg, torch, device, matrix: str = "c3", rhs: str = "ones", formats=None, target_iters: int = 0,
+          restart: int = 100, tol: float = 1e-10, max_iters: int = 20000, hist_every: int = 25):
+    """The basis-format sweep (iteration ratios against the fp64 basis, implicit-RRN histories and
+    per-block exponent spreads of the Krylov vectors) on c3 (256^3 convection-diffusion) or c4 (4M
+    power-law). rhs "ones": b = A 1; "sin": b = A x_sol with x_sol = s / ||s||, s_i = sin(i), the
+    Methodology's right-hand side. target_iters > 0 takes the Methodology's stopping protocol: the
+    RRN reached by target_iters iterations of fp64-basis GMRES, times 1.1, is every format's
+    tolerance."""
+    import workloads
+
+    formats = formats or ALL_FORMATS
+    if matrix == "c4":
+        A = workloads.powerlaw(1 << 22, seed=2, device=device)
+    else:
+        A = workloads.convdiff(256, 3, (1.0, 1.0, 1.0), 50.0, device=device)
+    if rhs == "sin":
+        s_ = workloads.sin_vector(A.n, device=device)
+        xs = s_ / torch.linalg.vector_norm(s_)
+    else:
+        xs = torch.ones(A.n, dtype=torch.float64, device=device)
+    b = pkg.spmv(A.row_ptr, A.col, A.vals, xs).clone()
+    out = {"matrix": matrix, "n": A.n, "nnz": A.nnz, "rhs": rhs, "restart": restart}
+    if target_iters > 0:
+        S = pkg.Solver(A.row_ptr, A.col, A.vals, restart=restart, tol=1e-300, fmt="fp64", max_iters=target_iters)
+        x = torch.zeros(A.n, dtype=torch.float64, device=device)
+        r64 = S.solve(b, x)
+        S.close()
+        tol = 1.1 * r64.true_rrn
+        out["target_protocol"] = {"fp64_iters": r64.iters, "fp64_rrn": r64.true_rrn, "tol": tol}
+    out["tol"] = tol
+    for f in formats:
+        fmt, bits = (f.split("_")[0], int(f.split("_")[1])) if f.startswith("frsz2") else (f, 32)
+        S = pkg.Solver(A.row_ptr, A.col, A.vals, restart=restart, tol=tol, fmt=fmt, frsz2_bits=bits,
+                       max_iters=max_iters, history=1)
+        x = torch.zeros(A.n, dtype=torch.float64, device=device)
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        r = S.solve(b, x)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t
+        h = S.history()
+        res = {"seconds": dt, "iters": r.iters, "restarts": r.restarts, "reorths": r.reorths,
+               "converged": r.converged, "true_rrn": r.true_rrn,
+               "x_rel_error": float(torch.linalg.vector_norm(x - xs) / torch.linalg.vector_norm(xs)),
+               "rrn_history": [[k + 1, float(h[k])] for k in range(hist_every - 1, len(h), hist_every)]}
+        if f in ("fp64", "frsz2_32") and r.iters > 0:
+            m_last = r.iters - (r.restarts - 1) * restart if r.restarts > 0 else r.iters
+            m_last = max(1, min(restart, m_last))  # slots 0 .. m_last - 1 hold the last cycle's basis
+            res["exponent_spread"] = {str(k): exponent_spread(S.basis_vector(k).cpu().numpy())
+                                      for k in sorted({0, m_last // 2, m_last - 1})}
+        S.close()
+        out[f] = res
+        del x
+        torch.cuda.empty_cache()
+    if "fp64" in out:
+        out["iteration_ratio_vs_fp64"] = {f: out[f]["iters"] / max(out["fp64"]["iters"], 1) for f in formats}
+        out["time_ratio_vs_fp64"] = {f: out[f]["seconds"] / out["fp64"]["seconds"] for f in formats}
     return out
 
 
@@ -450,6 +552,12 @@ def main():
     ap.add_argument("--serving-nmax", type=float, default=1e6, help="largest request n of the serving leg")
     ap.add_argument("--solve-c3", default="", help="comma-separated basis formats (fp64, fp32, fp16, bf16, "
                     "frsz2_16, frsz2_21, frsz2_32): run only the full 256^3 solves to 1e-10 and print them")
+    ap.add_argument("--solve-c4", default="", help="as --solve-c3, on the 4M-row power-law matrix")
+    ap.add_argument("--sweep", default="", choices=["", "c3", "c4"],
+                    help="run only the basis-format sweep (iteration ratios, RRN histories, exponent spreads)")
+    ap.add_argument("--rhs", default="ones", choices=["ones", "sin"], help="right-hand side of --sweep")
+    ap.add_argument("--target-iters", type=int, default=0,
+                    help="--sweep tolerance from this many fp64-basis iterations (the target-RRN protocol)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -492,9 +600,19 @@ def main():
     device = torch.device("cuda", local if world > 1 else torch.cuda.current_device())
     torch.cuda.set_device(device)
     peak, peak_src = load_peaks()
-    if args.solve_c3:
+    if args.sweep:
         if rank == 0:
-            print(json.dumps({"solve_c3": solve_c3(pkg, torch, device, args.solve_c3.split(","))}))
+            print(json.dumps({"sweep": sweep(pkg, torch, device, args.sweep, args.rhs, target_iters=args.target_iters)}))
+        if dist:
+            dist.barrier()
+            dist.destroy_process_group()
+        return
+    if args.solve_c3 or args.solve_c4:
+        if rank == 0:
+            if args.solve_c3:
+                print(json.dumps({"solve_c3": solve_c3(pkg, torch, device, args.solve_c3.split(","))}))
+            if args.solve_c4:
+                print(json.dumps({"solve_c4": solve_c3(pkg, torch, device, args.solve_c4.split(","), matrix="c4")}))
         if dist:
             dist.barrier()
             dist.destroy_process_group()

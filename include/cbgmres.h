@@ -277,6 +277,14 @@ int cbg_server_destroy(cbg_server* server);
 /* Copies up to cap recorded implicit relative residuals (opts.history != 0) to h_out. */
 int cbgmres_history(cbg_ctx* ctx, double* h_out, int64_t cap, int64_t* count);
 
+/* Decodes basis vector `slot` (0 <= slot <= restart) of the context's current Krylov basis, as
+ * stored in opts.fmt, into d_out (n doubles, device) on the context's stream; the call does not
+ * wait. After a finished solve, slots 0 .. m-1 hold the m vectors v_1 .. v_m of the last cycle
+ * (Fig. 1, decompressed as step 5 reads them). v_{m+1} of the cycle's last step is not stored,
+ * because the restart never reads it, and later slots are unspecified. For inspection (value and
+ * exponent distributions of the basis), not part of the solve. */
+int cbgmres_basis_vector(cbg_ctx* ctx, int32_t slot, double* d_out);
+
 /* Frees the context's device memory. Accepts NULL. */
 int cbgmres_destroy(cbg_ctx* ctx);
 

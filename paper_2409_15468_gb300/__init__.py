@@ -27,7 +27,7 @@ EXPORTS = ["cbg_frsz2_bytes", "cbg_frsz2_compress", "cbg_frsz2_decompress", "cbg
            "cbg_csr_validate",
            "cbg_spmv_work_bytes", "cbg_spmv", "cbg_opts_default", "cbgmres_workspace_bytes", "cbgmres_create",
            "cbgmres_solve", "cbgmres_start", "cbgmres_advance", "cbgmres_finish", "cbgmres_history",
-           "cbgmres_destroy", "cbg_server_create", "cbg_server_submit", "cbg_server_poll", "cbg_server_stats",
+           "cbgmres_destroy", "cbgmres_basis_vector", "cbg_server_create", "cbg_server_submit", "cbg_server_poll", "cbg_server_stats",
            "cbg_server_clock", "cbg_server_destroy", "cbg_last_error", "cbg_version"]
 
 
@@ -111,6 +111,7 @@ def load(path: str | None = None):
         "cbgmres_finish": (c_int, [P, ctypes.POINTER(Result)]),
         "cbgmres_history": (c_int, [P, P, i64, ctypes.POINTER(i64)]),
         "cbgmres_destroy": (c_int, [P]),
+        "cbgmres_basis_vector": (c_int, [P, i32, P]),
         "cbg_server_create": (c_int, [ctypes.POINTER(P), sz, i32, i32, i32]),
         "cbg_server_submit": (c_int, [P, ctypes.POINTER(Request)]),
         "cbg_server_poll": (c_int, [P, ctypes.POINTER(Completion), i32, ctypes.POINTER(i32)]),
@@ -346,6 +347,14 @@ class Solver:
         cnt = ctypes.c_int64(0)
         check(lib().cbgmres_history(self.handle, ctypes.c_void_p(buf.ctypes.data), cap, ctypes.byref(cnt)))
         return buf[: cnt.value]
+
+    def basis_vector(self, slot: int, out: torch.Tensor | None = None) -> torch.Tensor:
+        """Basis vector `slot` of the context's current Krylov basis, decoded (ordered on the
+        solver's stream; the returned tensor is ready once that stream has run)."""
+        if out is None:
+            out = torch.empty(max(self.n, 1), dtype=torch.float64, device="cuda")
+        check(lib().cbgmres_basis_vector(self.handle, slot, _ptr(out)))
+        return out[: self.n]
 
     def close(self):
         if getattr(self, "handle", None):

@@ -798,6 +798,22 @@ int cbgmres_history(cbg_ctx* c, double* h_out, int64_t cap, int64_t* count) {
   return CBG_OK;
 }
 
+int cbgmres_basis_vector(cbg_ctx* c, int32_t slot, double* d_out) {
+  if (!c || !d_out) {
+    set_error("cbgmres_basis_vector: null argument");
+    return CBG_ERR_INVALID_ARG;
+  }
+  if (slot < 0 || slot > c->opts.restart) {
+    set_error("cbgmres_basis_vector: slot %d outside [0, %d]", slot, c->opts.restart);
+    return CBG_ERR_INVALID_ARG;
+  }
+  if (c->phase == kValidating) {
+    set_error("cbgmres_basis_vector: the context has not been validated yet");
+    return CBG_ERR_STATE;
+  }
+  return launch_load(view_of(c), slot, d_out, c->stream);
+}
+
 int cbgmres_destroy(cbg_ctx* c) {
   ctx_release(c);
   return CBG_OK;

@@ -179,3 +179,27 @@ def test_gmres_powerlaw_parity(cbg, orc):
     assert abs(r.iters - ref.iters) <= max(1, 0.02 * ref.iters)
     xo = ref.x
     assert np.linalg.norm(x.cpu().numpy() - xo) / np.linalg.norm(xo) <= 1e-8
+
+
+@pytest.mark.parametrize("fmt,l,bound", [("fp64", 32, 1e-12), ("frsz2", 32, 1e-7)])
+def test_basis_vector_orthonormal(cbg, fmt, l, bound):
+    """cbgmres_basis_vector returns the stored Krylov basis: after one cycle of 12 steps the 12
+    decoded vectors v_1 .. v_12 are orthonormal to the precision of their storage format."""
+    A, xt = c1()
+    Ad = A.to("cuda")
+    b = cbg.spmv(Ad.row_ptr, Ad.col, Ad.vals, xt.cuda()).clone()
+    S = cbg.Solver(Ad.row_ptr, Ad.col, Ad.vals, restart=20, tol=1e-14, fmt=fmt, frsz2_bits=l, max_iters=12)
+    x = torch.zeros(A.n, dtype=torch.float64, device="cuda")
+    r = S.solve(b, x)
+    assert r.iters == 12
+    V = torch.stack([S.basis_vector(k).clone() for k in range(12)])
+    torch.cuda.synchronize()
+    S.close()
+    G = (V @ V.T).cpu().numpy()
+    assert np.abs(G - np.eye(12)).max() <= bound
+    with pytest.raises(cbg.CbgError):
+        S2 = cbg.Solver(Ad.row_ptr, Ad.col, Ad.vals, restart=20)
+        try:
+            S2.basis_vector(21)
+        finally:
+            S2.close()
