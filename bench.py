@@ -399,6 +399,49 @@ def sweep(pkg, torch, device, matrix: str = "c3", rhs: str = "ones", formats=Non
     return out
 
 
+INTENSITY_R = [0, 1, 2, 3, 4, 5, 6, 7, 8, 10, 12, 14, 16, 20, 24, 28, 32, 40, 48, 56, 64, 80, 96, 112, 128, 192, 256]
+
+
+def intensity_sweep(pkg, torch, device, n: int = 1 << 28, runs: int = 10, peak_gbs: float = 0.0):
+    """The synthetic arithmetic-intensity benchmark (Fig. 3 protocol): 2^28 stored values per
+    format, 27 settings of r fused multiply-adds per value, the minimum of 10 runs each (CUDA
+    events). Per value 2r + 1 floating-point operations over the format's bytes per value."""
+    import workloads
+
+    variants = [("fp64", 32, False), ("fp32", 32, True), ("fp32", 32, False), ("fp16", 32, False),
+                ("bf16", 32, False), ("frsz2", 16, False), ("frsz2", 21, False), ("frsz2", 32, False)]
+    x = workloads.basis_vector(0, n, seed=1, device=device)
+    out = {"n": n, "runs": runs, "r": INTENSITY_R,
+           "roofs": {"hbm_gbs": peak_gbs, "fp64_gflops_probe": 2 * 599.4,
+                     "fp64_note": "DFMA 599 G op/s measured on this pool's GB300 by an FMA-chain probe",
+                     "fp32_gflops_probe": 2 * 37477.0}}
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    for fmt, l, native in variants:
+        B = pkg.BasisStorage(n, 1, pkg.FORMATS[fmt], l)
+        B.store(0, x)
+        vb = stored_bytes(fmt, l, n)
+        res = torch.empty(1, dtype=torch.float64, device=device)
+        work = B.work(1)
+        rows = []
+        for r in INTENSITY_R:
+            B.intensity(0, r, fp32_compute=native, out=res, work=work)
+            best = float("inf")
+            for _ in range(runs):
+                e0.record()
+                B.intensity(0, r, fp32_compute=native, out=res, work=work)
+                e1.record()
+                torch.cuda.synchronize()
+                best = min(best, e0.elapsed_time(e1))
+            flops = n * (2 * r + 1)
+            rows.append({"r": r, "flop_per_byte": flops / vb, "gflops": flops / (best * 1e-3) / 1e9,
+                         "gbs": vb / (best * 1e-3) / 1e9, "ms": best})
+        name = (fmt if fmt != "frsz2" else f"frsz2_{l}") + ("_native_fp32" if native else "")
+        out[name] = rows
+        del B, work
+        torch.cuda.empty_cache()
+    return out
+
+
 def serving(pkg, torch, device, count: int, n_min: float, n_max: float, budget_gb: float = 96.0,
             max_active: int = 16, steps_per_turn: int = 8, restart: int = 100, seed: int = 3):
     """The serving workload: a Poisson stream of convection-diffusion solves (n log-uniform in
@@ -556,6 +599,8 @@ def main():
     ap.add_argument("--sweep", default="", choices=["", "c3", "c4"],
                     help="run only the basis-format sweep (iteration ratios, RRN histories, exponent spreads)")
     ap.add_argument("--rhs", default="ones", choices=["ones", "sin"], help="right-hand side of --sweep")
+    ap.add_argument("--intensity", action="store_true",
+                    help="run only the arithmetic-intensity sweep of the stored formats (Fig. 3 protocol)")
     ap.add_argument("--target-iters", type=int, default=0,
                     help="--sweep tolerance from this many fp64-basis iterations (the target-RRN protocol)")
     args = ap.parse_args()
@@ -600,6 +645,13 @@ def main():
     device = torch.device("cuda", local if world > 1 else torch.cuda.current_device())
     torch.cuda.set_device(device)
     peak, peak_src = load_peaks()
+    if args.intensity:
+        if rank == 0:
+            print(json.dumps({"intensity": intensity_sweep(pkg, torch, device, peak_gbs=peak)}))
+        if dist:
+            dist.barrier()
+            dist.destroy_process_group()
+        return
     if args.sweep:
         if rank == 0:
             print(json.dumps({"sweep": sweep(pkg, torch, device, args.sweep, args.rhs, target_iters=args.target_iters)}))

@@ -132,6 +132,18 @@ int cbg_basis_dot_noalloc(const cbg_basis* basis, int32_t nvec, const double* d_
 int cbg_basis_update(const cbg_basis* basis, int32_t nvec, const double* d_h, double* d_w, double* d_norm2,
                      void* d_work, size_t work_bytes, void* stream);
 
+/* The synthetic arithmetic-intensity benchmark of the synthetic-performance discussion (Fig. 3):
+ * every value x_k of stored vector `slot` is read and decoded to FP64 (as cbg_basis_load does),
+ * then r = fma_per_value fused multiply-adds f(y) = 0.5 y + 0.25 are applied to it, and
+ * *d_out = sum_k f^r(x_k) (FP64, fixed reduction order). The multiplication by 0.5 is exact, so
+ * every step rounds once. compute_fp32 != 0 (fmt CBG_FP32 only) reads the binary32 values and
+ * computes and sums in FP32 per thread, the paper's native float baseline. Per value: 2 r + 1
+ * floating-point operations over the format's bytes per value. d_work as for cbg_basis_dot with
+ * nvec = 1. Errors: CBG_ERR_INVALID_ARG (bad basis, slot < 0, r < 0 or > 2^20, compute_fp32 on
+ * another format). */
+int cbg_intensity(const cbg_basis* basis, int32_t slot, int32_t fma_per_value, int32_t compute_fp32, double* d_out,
+                  void* d_work, size_t work_bytes, void* stream);
+
 /* ---- sparse matrix ---------------------------------------------------------------------------- */
 /* Checks a CSR matrix on the device: row_ptr[0] == 0, row_ptr[n] == nnz, row pointers monotone,
  * every column in [0, n). Returns CBG_ERR_BAD_MATRIX otherwise. Synchronises the stream.

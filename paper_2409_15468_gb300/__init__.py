@@ -23,7 +23,7 @@ ERR_NOT_CONVERGED = -5
 
 # Symbols declared in include/cbgmres.h (checked by the CPU tests).
 EXPORTS = ["cbg_frsz2_bytes", "cbg_frsz2_compress", "cbg_frsz2_decompress", "cbg_basis_layout", "cbg_basis_store",
-           "cbg_basis_load", "cbg_basis_work_bytes", "cbg_basis_dot", "cbg_basis_dot_noalloc", "cbg_basis_update",
+           "cbg_basis_load", "cbg_basis_work_bytes", "cbg_basis_dot", "cbg_basis_dot_noalloc", "cbg_basis_update", "cbg_intensity",
            "cbg_csr_validate",
            "cbg_spmv_work_bytes", "cbg_spmv", "cbg_opts_default", "cbgmres_workspace_bytes", "cbgmres_create",
            "cbgmres_solve", "cbgmres_start", "cbgmres_advance", "cbgmres_finish", "cbgmres_history",
@@ -99,6 +99,7 @@ def load(path: str | None = None):
         "cbg_basis_dot": (c_int, [ctypes.POINTER(Basis), i32, P, P, P, sz, P]),
         "cbg_basis_dot_noalloc": (c_int, [ctypes.POINTER(Basis), i32, P, P, P]),
         "cbg_basis_update": (c_int, [ctypes.POINTER(Basis), i32, P, P, P, P, sz, P]),
+        "cbg_intensity": (c_int, [ctypes.POINTER(Basis), i32, i32, i32, P, P, sz, P]),
         "cbg_csr_validate": (c_int, [i32, i64, P, P, P]),
         "cbg_spmv_work_bytes": (sz, [i32]),
         "cbg_spmv": (c_int, [i32, i64, P, P, P, P, P, P, P, sz, P]),
@@ -249,6 +250,17 @@ class BasisStorage:
         check(lib().cbg_basis_update(ctypes.byref(self.struct), nvec, _ptr(h), _ptr(w), _ptr(norm2), _ptr(work),
                                      work.numel(), _stream(stream)))
         return w
+
+
+    def intensity(self, slot: int, fma_per_value: int, fp32_compute: bool = False, out: torch.Tensor | None = None,
+                  work: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+        """sum_k f^r(x_k) over stored vector `slot`, f(y) = 0.5 y + 0.25 (cbg_intensity)."""
+        if out is None:
+            out = torch.empty(1, dtype=torch.float64, device=self.vals.device)
+        work = work if work is not None else self.work(1)
+        check(lib().cbg_intensity(ctypes.byref(self.struct), slot, fma_per_value, int(fp32_compute), _ptr(out),
+                                  _ptr(work), work.numel(), _stream(stream)))
+        return out
 
 
 # ---------------------------------------------------------------------------------------------

@@ -8,42 +8,13 @@
 #include <unordered_map>
 
 #include "basis_common.cuh"
+#include "decode.cuh"
 
 namespace cbg {
 
 // ------------------------------------------------------------------------------------------------
 // Cast formats: widen to FP64 with integer operations, one FP64 FMA per element and vector
 // ------------------------------------------------------------------------------------------------
-
-__device__ __forceinline__ double widen_f32(uint32_t f) {
-  const uint32_t e = (f >> 23) & 0xFFu, m = f & 0x7FFFFFu;
-  const uint64_t sgn = static_cast<uint64_t>(f >> 31) << 63;
-  uint64_t d;
-  if (e != 0) {
-    d = sgn | (static_cast<uint64_t>(e + 896) << 52) | (static_cast<uint64_t>(m) << 29);
-  } else if (m == 0) {
-    d = sgn;
-  } else {  // subnormal m 2^-149: normalise with the position p of its leading 1
-    const int p = 31 - __clz(m);
-    d = sgn | (static_cast<uint64_t>(p + 874) << 52) | (static_cast<uint64_t>(m ^ (1u << p)) << (52 - p));
-  }
-  return __longlong_as_double(static_cast<long long>(d));
-}
-
-__device__ __forceinline__ double widen_f16(uint32_t h) {
-  const uint32_t e = (h >> 10) & 0x1Fu, m = h & 0x3FFu;
-  const uint64_t sgn = static_cast<uint64_t>((h >> 15) & 1u) << 63;
-  uint64_t d;
-  if (e != 0) {
-    d = sgn | (static_cast<uint64_t>(e + 1008) << 52) | (static_cast<uint64_t>(m) << 42);
-  } else if (m == 0) {
-    d = sgn;
-  } else {  // subnormal m 2^-24
-    const int p = 31 - __clz(m);
-    d = sgn | (static_cast<uint64_t>(p + 999) << 52) | (static_cast<uint64_t>(m ^ (1u << p)) << (52 - p));
-  }
-  return __longlong_as_double(static_cast<long long>(d));
-}
 
 template <int F>
 struct CastTraits;

@@ -296,6 +296,28 @@ int cbg_basis_update(const cbg_basis* basis, int32_t nvec, const double* d_h, do
                              Gate{nullptr, nullptr}, s);
 }
 
+int cbg_intensity(const cbg_basis* basis, int32_t slot, int32_t fma_per_value, int32_t compute_fp32, double* d_out,
+                  void* d_work, size_t work_bytes, void* stream) {
+  int st = check_basis(basis, 1);
+  if (st) return st;
+  if (slot < 0) return bad("cbg_intensity: negative slot");
+  if (fma_per_value < 0 || fma_per_value > (1 << 20)) return bad("cbg_intensity: fma_per_value outside [0, 2^20]");
+  if (compute_fp32 && basis->fmt != CBG_FP32) return bad("cbg_intensity: compute_fp32 needs fp32 storage");
+  if (!d_out || !aligned(d_out, 8)) return bad("cbg_intensity: bad output pointer");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (basis->n == 0) {
+    cudaError_t e = cudaMemsetAsync(d_out, 0, sizeof(double), s);
+    return e == cudaSuccess ? CBG_OK : cuda_fail(e, "cbg_intensity: zero fill");
+  }
+  DeviceInfo di;
+  st = device_info(&di);
+  if (st) return st;
+  Work w;
+  st = take_work(d_work, work_bytes, 1, s, &w);
+  if (st) return st;
+  return launch_intensity(view(basis), slot, fma_per_value, compute_fp32 != 0, w.partials, w.counter, d_out, s);
+}
+
 int cbg_csr_validate(int32_t n, int64_t nnz, const int32_t* d_row_ptr, const int32_t* d_col, void* stream) {
   if (n < 1 || nnz < 0 || nnz > INT32_MAX) return bad("cbg_csr_validate: n or nnz out of range");
   if (!d_row_ptr || (nnz > 0 && !d_col)) return bad("cbg_csr_validate: null pointer");

@@ -14,6 +14,7 @@
 #include <cuda_fp16.h>
 
 #include "common.cuh"
+#include "decode.cuh"
 #include "kernels.cuh"
 
 namespace cbg {
@@ -96,40 +97,7 @@ __global__ void __launch_bounds__(256) k_frsz2_compress(const double* __restrict
   }
 }
 
-// Decompression steps 1-4 for the value at index k.
-template <int L>
-__device__ __forceinline__ double frsz2_decode(const uint32_t* __restrict__ exps, const uint32_t* __restrict__ codes,
-                                               int64_t k) {
-  const int64_t b = k >> 5;
-  const int i = static_cast<int>(k & 31);
-  const uint32_t emax = exps[b];  // step 1
-  uint32_t c;
-  if (L == 32) {
-    c = codes[b * 32 + i];
-  } else if (L == 16) {
-    c = reinterpret_cast<const uint16_t*>(codes)[b * 32 + i];
-  } else {
-    const int bit = 21 * i, a = bit >> 5;
-    const uint32_t lo = codes[b * 21 + a];
-    const uint32_t hi = a + 1 < 21 ? codes[b * 21 + a + 1] : 0u;
-    c = __funnelshift_r(lo, hi, bit & 31) & 0x1FFFFFu;
-  }
-  const uint64_t s = c >> (L - 1);  // step 2: sign and significand
-  const uint32_t S = c & ((1u << (L - 1)) - 1u);
-  if (S == 0) return __longlong_as_double(static_cast<long long>(s << 63));
-  const int ebar = emax > 1 ? static_cast<int>(emax) : 1;
-  const int k0 = __clz(S) - (32 - (L - 1));  // step 2: inserted zeros
-  const int p = L - 2 - k0;                   // position of the leading 1
-  const int e = ebar - k0;                    // step 3: e = e_max - k
-  uint64_t bits;
-  if (e >= 1) {  // step 4: reassemble; the leading 1 becomes implicit again
-    bits = (s << 63) | (static_cast<uint64_t>(e) << 52) | (static_cast<uint64_t>(S ^ (1u << p)) << (52 - p));
-  } else {       // below the normal range: an IEEE subnormal S * 2^(ebar - 1023 - (l-2))
-    bits = (s << 63) | (static_cast<uint64_t>(S) << (ebar + 53 - L));
-  }
-  return __longlong_as_double(static_cast<long long>(bits));
-}
-
+// Decompression steps 1-4 (frsz2_decode), one value per thread.
 template <int L>
 __global__ void k_frsz2_decompress(const uint32_t* __restrict__ exps, const uint32_t* __restrict__ codes, int64_t n,
                                    double* __restrict__ dst) {

@@ -114,6 +114,11 @@ struct GivensArgs {
 int launch_givens(const GivensArgs& a, int j, cudaStream_t stream);
 int launch_cycle_init(SolverCtl* ctl, double* g, int m, int steps_allowed, cudaStream_t stream);
 
+// ---- intensity.cu -------------------------------------------------------------------------------
+// *out = sum_k f^r(x_k) over stored vector `slot` (see cbg_intensity). partials: kMaxGrid doubles.
+int launch_intensity(const BasisView& B, int slot, int r, bool fp32_compute, double* partials, unsigned int* counter,
+                     double* out, cudaStream_t stream);
+
 // ---- solver contexts over caller-provided memory (solver.cu), used by the serving runtime ----
 size_t ctx_pinned_bytes();
 size_t ctx_device_bytes(int32_t n, const cbg_opts* opts);

@@ -106,3 +106,26 @@ def test_dot_after_update_orthogonal(cbg, orc):
     B.update(nvec, h, w)
     h2 = B.dot(nvec, w).cpu().numpy()
     assert np.abs(h2).max() <= 1e-13 * np.linalg.norm(h.cpu().numpy())
+
+
+@pytest.mark.parametrize("fmt,l", FORMATS)
+@pytest.mark.parametrize("r", [0, 1, 7])
+def test_intensity(cbg, orc, fmt, l, r):
+    """cbg_intensity (the synthetic benchmark of Fig. 3): sum_k f^r(x_k), f(y) = y/2 + 1/4, over the
+    oracle-decoded stored values. Each f step is exact up to one rounding on both sides, so the
+    values agree bit for bit and only the order of the final sum differs."""
+    n = 4096 * 3 + 45
+    B, Vhat, _ = make_basis(cbg, orc, n, 2, fmt, l, seed=11)
+    y = Vhat[1].copy()
+    for _ in range(r):
+        y = y * 0.5 + 0.25
+    ref = orc.dot2(y, np.ones(n))
+    got = B.intensity(1, r).item()
+    assert abs(got - ref) <= n * 2.0 ** -52 * np.abs(y).sum() + 1e-300
+    if fmt == 1:  # fp32 storage computed natively in FP32
+        y32 = Vhat[1].astype(np.float32)
+        for _ in range(r):
+            y32 = y32 * np.float32(0.5) + np.float32(0.25)
+        ref32 = orc.dot2(y32.astype(np.float64), np.ones(n))
+        got32 = B.intensity(1, r, fp32_compute=True).item()
+        assert abs(got32 - ref32) <= 8 * 2.0 ** -24 * np.abs(y32.astype(np.float64)).sum()
