@@ -315,23 +315,24 @@ __global__ void __launch_bounds__(FDot<L>::kThreads) k_dot_frsz2(BasisView B, in
 }
 
 // ================================================================================================
-// update: 8 consecutive values per thread, 4 threads per block, 32 blocks per tile, two basis vectors
-// per pipeline stage, vectors in groups of at most 32 (the exact integer sums are per group)
+// update: 8 consecutive values per thread, 4 threads per block, 32 blocks per tile, four basis
+// vectors per pipeline stage, vectors in groups of at most 32 (the exact integer sums are per group)
 // ================================================================================================
 
-// S pipeline stages: 3 when the grid fills the GPU (occupancy matters); 12 when it does not (small
-// n: each CTA then has little work per stage, and only more copies in flight hide the latency).
-template <int L, int S = 3>
+// S pipeline stages of 4 vectors: 2 when the grid fills the GPU (occupancy matters); 12 when it
+// does not (small n: each CTA then has little work per stage, and only more copies in flight hide
+// the latency).
+template <int L, int S = 2>
 struct FUpd {
   static constexpr int kThreads = 128;
   static constexpr int kWarps = 4;
   static constexpr int kBlocks = 32;
-  static constexpr int kVps = 2;  // basis vectors per stage
+  static constexpr int kVps = 4;  // basis vectors per stage
   static constexpr int kStages = S;
   static constexpr int kGroup = 32;
   // resident CTAs per SM the register allocation is capped for (l < 32 is faster with a few spills
   // and one more CTA); the deep pipeline runs one CTA per SM
-  static constexpr int kMinBlocks = S != 3 ? 1 : (L == 32 ? 5 : 6);
+  static constexpr int kMinBlocks = S == 12 ? 1 : (L == 32 ? 5 : 6);
   static constexpr int kVecBytes = kBlocks * L * 4;
   static constexpr int kStageBytes = kVps * kVecBytes;
   // dynamic smem: stages | coefficient table [kGroup][kBlocks] (int2) | exponent words of one group
@@ -574,7 +575,7 @@ __global__ void __launch_bounds__(FUpd<L, SD>::kThreads, FUpd<L, SD>::kMinBlocks
           const uint8_t* st = stages + s * C::kStageBytes;
 #pragma unroll
           for (int j = 0; j < VPS; ++j) {
-            if (j == 0 || v + 1 < gn) {
+            if (v + j < gn) {
               uint32_t c[8];
               load_codes8<L>(reinterpret_cast<const uint32_t*>(st + j * C::kVecBytes), t, c);
               const int2 gp = gam[(v + j) * NBT + blk];
@@ -756,7 +757,7 @@ int frsz2_update_launch_l(const BasisView& B, int nvec, const int* nvec_dev, con
   const int64_t need = ((B.n + 31) / 32 + 7) / 8;
   if (need < di.sms)
     return frsz2_update_launch_t<L, 12>(B, nvec, nvec_dev, h, negate, w, partials, counter, err, epi, gate, 0, stream);
-  return frsz2_update_launch_t<L, 3>(B, nvec, nvec_dev, h, negate, w, partials, counter, err, epi, gate, 0, stream);
+  return frsz2_update_launch_t<L, 2>(B, nvec, nvec_dev, h, negate, w, partials, counter, err, epi, gate, 0, stream);
 }
 
 }  // namespace

@@ -6,7 +6,7 @@
 // One thread per row for short rows: the stencil matrices have ~7 nonzeros per row, so the rows of a
 // warp cover a contiguous stretch of the value and column arrays that L1 serves to the per-nonzero
 // loads, and the FP64 work is exactly one FMA per nonzero (GB300's FP64 rate is the other bound of
-// this kernel). Matrices with long rows (mean >= 12 nonzeros) use G lanes per row instead.
+// this kernel). Matrices with long rows (mean >= 12 nonzeros) use 4 lanes per row instead.
 // Rows are strided over a grid sized to the SM count so that the norm partials stay few.
 #include "common.cuh"
 #include "kernels.cuh"
@@ -61,9 +61,10 @@ __global__ void __launch_bounds__(256) k_spmv(int n, const int32_t* __restrict__
 // Rows with many nonzeros (power-law matrices): G consecutive lanes per row, so the loads of a
 // row's values and column indices are coalesced and a long row is split G ways. Each lane issues
 // U independent (column, value, x-gather) loads before it uses any of them, and the next row's
-// bounds are loaded before the current row is processed: the kernel is bound by load latency,
-// so it keeps several gathers in flight per lane. The lane's U partial sums and the G lanes of a
-// row are combined in a fixed order (deterministic).
+// bounds are loaded before the current row is processed, so several gathers are in flight per
+// lane. Each lane keeps one FMA chain and the G lanes of a row combine in a fixed shuffle order
+// (deterministic): on GB300 every extra FP64 add costs as much issue time as a gather, so the
+// combining work is kept to log2(G) adds per row and lane.
 template <int G, int U>
 __global__ void __launch_bounds__(256) k_spmv_vec(int n, const int32_t* __restrict__ row_ptr,
                                                   const int32_t* __restrict__ col, const double* __restrict__ vals,
@@ -94,9 +95,7 @@ __global__ void __launch_bounds__(256) k_spmv_vec(int n, const int32_t* __restri
       q0 = __ldg(row_ptr + inext);
       q1 = __ldg(row_ptr + inext + 1);
     }
-    double acc[U];
-#pragma unroll
-    for (int u = 0; u < U; ++u) acc[u] = 0.0;
+    double s = 0.0;  // one chain: the loads of a pass are in flight before its first FMA
     for (int p = p0 + sub; p < p1; p += G * U) {
       int c[U];
       double v[U];
@@ -110,11 +109,8 @@ __global__ void __launch_bounds__(256) k_spmv_vec(int n, const int32_t* __restri
 #pragma unroll
       for (int u = 0; u < U; ++u) xv[u] = c[u] >= 0 ? __ldg(x + c[u]) : 0.0;
 #pragma unroll
-      for (int u = 0; u < U; ++u) acc[u] = fma(v[u], xv[u], acc[u]);
+      for (int u = 0; u < U; ++u) s = fma(v[u], xv[u], s);
     }
-    double s = acc[0];
-#pragma unroll
-    for (int u = 1; u < U; ++u) s += acc[u];
 #pragma unroll
     for (int o = G / 2; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
     if (i < n && sub == 0) {
@@ -198,11 +194,11 @@ int grid_rows(int64_t n, int per_sm) {
 }  // namespace
 
 // Lanes per row from the mean row length: one thread per row below 12 nonzeros per row
-// (stencils); 8 lanes (4 loads each in flight) below 48; 16 lanes above.
+// (stencils), else 4 lanes with 8 loads each in flight (measured best for mean row lengths 29 and
+// 56 among 2-32 lanes and 2-8 loads).
 int spmv_lanes_per_row(int n, int64_t nnz) {
   const double mean = n > 0 ? static_cast<double>(nnz) / n : 0.0;
-  if (mean < 12.0) return 1;
-  return mean < 48.0 ? 8 : 16;
+  return mean < 12.0 ? 1 : 4;
 }
 
 int launch_spmv(int n, int64_t nnz, const int32_t* row_ptr, const int32_t* col, const double* vals, const double* x,
@@ -215,10 +211,7 @@ int launch_spmv(int n, int64_t nnz, const int32_t* row_ptr, const int32_t* col, 
     k_spmv<<<grid, 256, 0, stream>>>(n, row_ptr, col, vals, x, y, bsub, partials, counter, err, epi, gate);
   } else {
     const int grid = grid_rows((int64_t)n * g, 8);
-    if (g == 8)
-      k_spmv_vec<8, 4><<<grid, 256, 0, stream>>>(n, row_ptr, col, vals, x, y, bsub, partials, counter, err, epi, gate);
-    else
-      k_spmv_vec<16, 4><<<grid, 256, 0, stream>>>(n, row_ptr, col, vals, x, y, bsub, partials, counter, err, epi, gate);
+    k_spmv_vec<4, 8><<<grid, 256, 0, stream>>>(n, row_ptr, col, vals, x, y, bsub, partials, counter, err, epi, gate);
   }
   cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? CBG_OK : cuda_fail(e, "spmv launch");
