@@ -153,8 +153,8 @@ int cbg_csr_validate(int32_t n, int64_t nnz, const int32_t* d_row_ptr, const int
 /* d_y = A d_x for the CSR matrix (int32 row pointers and columns, FP64 values): Fig. 1 step 3,
  * w := A M^{-1} v with M = I (no preconditioner: Solver Configuration). If d_norm2 is not NULL it
  * receives ||y||^2 (step 4). nnz = row_ptr[n]; it chooses the kernel (one thread per row for
- * short rows, 4 to 32 lanes per row when the mean row length is 12 or more) and must match the
- * matrix. d_work: cbg_spmv_work_bytes(n) bytes. */
+ * short rows, 4 lanes per row when the mean row length is 12 or more) and must match the matrix.
+ * d_work: cbg_spmv_work_bytes(n) bytes. */
 size_t cbg_spmv_work_bytes(int32_t n);
 int cbg_spmv(int32_t n, int64_t nnz, const int32_t* d_row_ptr, const int32_t* d_col, const double* d_vals,
              const double* d_x, double* d_y, double* d_norm2, void* d_work, size_t work_bytes, void* stream);
@@ -168,7 +168,13 @@ typedef struct cbg_opts {
   double tol;         /* target relative residual ||b - A x|| / ||b|| (Eq. 4) */
   int64_t max_iters;  /* cap on Arnoldi steps */
   double eta;         /* re-orthogonalisation threshold of Fig. 1 step 7 (default 1/sqrt(2)) */
+  int32_t precond;    /* the M of Fig. 1 steps 3 and 17, applied on the right: CBG_PRECOND_NONE
+                         (M = I, the paper's setting, default) or CBG_PRECOND_JACOBI (M = diag(A);
+                         a zero or missing diagonal entry ends the solve with CBG_ERR_BAD_MATRIX) */
+  int32_t reserved_;  /* must be 0 */
 } cbg_opts;
+
+enum { CBG_PRECOND_NONE = 0, CBG_PRECOND_JACOBI = 1 };
 
 typedef struct cbg_result {
   int64_t iters;       /* Arnoldi steps (new basis vectors) */
@@ -183,7 +189,8 @@ typedef struct cbg_result {
 
 typedef struct cbg_ctx cbg_ctx;
 
-/* Fills defaults: restart 100, FRSZ2 with l = 32, tol 1e-10, max_iters 20000, eta 1/sqrt(2). */
+/* Fills defaults: restart 100, FRSZ2 with l = 32, tol 1e-10, max_iters 20000, eta 1/sqrt(2),
+ * no preconditioner. */
 int cbg_opts_default(cbg_opts* opts);
 
 /* Device bytes a context of size n with these options allocates (HBM admission control). */

@@ -46,7 +46,7 @@ _lib = None
 
 class _Opts(ctypes.Structure):
     _fields_ = [("restart", ctypes.c_int32), ("fmt", ctypes.c_int32), ("frsz2_bits", ctypes.c_int32),
-                ("pad_", ctypes.c_int32), ("tol", ctypes.c_double), ("max_iters", ctypes.c_int64),
+                ("precond", ctypes.c_int32), ("tol", ctypes.c_double), ("max_iters", ctypes.c_int64),
                 ("eta", ctypes.c_double)]
 
 
@@ -265,21 +265,27 @@ class GmresResult:
     hist_true: np.ndarray
 
 
-def _opts(restart, tol, max_iters, fmt, l, eta):
-    return _Opts(restart=restart, fmt=fmt, frsz2_bits=l, pad_=0, tol=tol, max_iters=max_iters, eta=eta)
+PRECOND = {"none": 0, "jacobi": 1}
+
+
+def _opts(restart, tol, max_iters, fmt, l, eta, precond="none"):
+    return _Opts(restart=restart, fmt=fmt, frsz2_bits=l, precond=PRECOND[precond], tol=tol, max_iters=max_iters,
+                 eta=eta)
 
 
 DEFAULT_ETA = 1.0 / np.sqrt(2.0)
 
 
 def gmres(row_ptr, col, vals, b, x0=None, *, restart=50, tol=1e-10, max_iters=20000, fmt=FP64, l=32,
-          eta=DEFAULT_ETA) -> GmresResult:
+          eta=DEFAULT_ETA, precond="none") -> GmresResult:
+    """Restarted (CB-)GMRES of Fig. 1 with the basis stored in `fmt`; precond "jacobi" applies
+    M = diag(A) on the right (steps 3 and 17), "none" is M = I."""
     row_ptr = np.ascontiguousarray(row_ptr, dtype=np.int32)
     col = np.ascontiguousarray(col, dtype=np.int32)
     vals, b = _f64(vals), _f64(b)
     n = row_ptr.size - 1
     x = np.zeros(n) if x0 is None else _f64(x0).copy()
-    o = _opts(restart, tol, max_iters, fmt, l, eta)
+    o = _opts(restart, tol, max_iters, fmt, l, eta, precond)
     r = _Result()
     hi = np.zeros(max(max_iters, 1))
     ht = np.zeros(max_iters + 2)

@@ -353,6 +353,7 @@ typedef struct {
   uint32_t* store_exp;  /* (m+1) FRSZ2 exponent arrays */
   double* vhat;         /* (m+1) x n decoded copies of the stored basis */
   double *v, *w, *h, *u, *H, *R, *cs, *sn, *g, *y;
+  double *dinv, *t; /* Jacobi: 1 / diag(A) and a scratch vector; NULL for M = I */
 } cycle_ws;
 
 /* Append v as basis vector `slot`: store it in the chosen format (Fig. 1 steps 1 and 14,
@@ -381,8 +382,13 @@ static int run_cycle(cycle_ws* ws, const double* r, double beta, double* x, int6
   ws->g[0] = beta;
   int m_eff = 0;
   for (int j = 0; j < m; ++j) {
-    /* Step 3: w := A v (M = I; v is the FP64 vector, the SpMV is not highlighted). */
-    orc_spmv_csr(n, ws->row_ptr, ws->col, ws->vals, ws->v, ws->w);
+    /* Step 3: w := A (M^{-1} v); v is the FP64 vector (the SpMV is not highlighted). */
+    if (ws->dinv) {
+      for (int32_t k = 0; k < n; ++k) ws->t[k] = ws->v[k] * ws->dinv[k];
+      orc_spmv_csr(n, ws->row_ptr, ws->col, ws->vals, ws->t, ws->w);
+    } else {
+      orc_spmv_csr(n, ws->row_ptr, ws->col, ws->vals, ws->v, ws->w);
+    }
     /* Step 4: omega := ||w||. */
     double omega = orc_nrm2(ws->w, n);
     /* Step 5: classical Gram-Schmidt against the stored (decoded) basis:
@@ -466,10 +472,19 @@ static int run_cycle(cycle_ws* ws, const double* r, double beta, double* x, int6
     for (int i = k + 1; i < mls; ++i) t -= ws->R[(size_t)i * ld + k] * ws->y[i];
     ws->y[k] = t / ws->R[(size_t)k * ld + k];
   }
-  /* x_m := x_0 + V_m y_m, reading the stored basis (highlighted). */
-  for (int i = 0; i < mls; ++i) {
-    const double* vi = ws->vhat + (size_t)i * n;
-    for (int32_t k = 0; k < n; ++k) x[k] += vi[k] * ws->y[i];
+  /* x_m := x_0 + M^{-1} (V_m y_m), reading the stored basis (highlighted). */
+  if (ws->dinv) {
+    for (int32_t k = 0; k < n; ++k) ws->t[k] = 0.0;
+    for (int i = 0; i < mls; ++i) {
+      const double* vi = ws->vhat + (size_t)i * n;
+      for (int32_t k = 0; k < n; ++k) ws->t[k] += vi[k] * ws->y[i];
+    }
+    for (int32_t k = 0; k < n; ++k) x[k] += ws->dinv[k] * ws->t[k];
+  } else {
+    for (int i = 0; i < mls; ++i) {
+      const double* vi = ws->vhat + (size_t)i * n;
+      for (int32_t k = 0; k < n; ++k) x[k] += vi[k] * ws->y[i];
+    }
   }
   return m_eff;
 }
@@ -508,6 +523,21 @@ static int ws_init(cycle_ws* ws, int32_t n, const int32_t* row_ptr, const int32_
   if (!ws->store || !ws->store_exp || !ws->vhat || !ws->v || !ws->w || !ws->h || !ws->u || !ws->H || !ws->R ||
       !ws->cs || !ws->sn || !ws->g || !ws->y)
     return -2;
+  if (o->precond == 1) {
+    /* Jacobi: M = diag(A), entries of row i in column i summed; M^{-1} stored as 1 / a_ii. */
+    ws->dinv = (double*)malloc((size_t)n * sizeof(double));
+    ws->t = (double*)malloc((size_t)n * sizeof(double));
+    if (!ws->dinv || !ws->t) return -2;
+    for (int32_t i = 0; i < n; ++i) {
+      double d = 0.0;
+      for (int32_t p = row_ptr[i]; p < row_ptr[i + 1]; ++p)
+        if (col[p] == i) d += vals[p];
+      if (d == 0.0 || !isfinite(d)) return -3;
+      ws->dinv[i] = 1.0 / d;
+    }
+  } else if (o->precond != 0) {
+    return -1;
+  }
   return 0;
 }
 
@@ -525,6 +555,8 @@ static void ws_free(cycle_ws* ws) {
   free(ws->sn);
   free(ws->g);
   free(ws->y);
+  free(ws->dinv);
+  free(ws->t);
 }
 
 /* r := b - A x (Fig. 1 step 1). */

@@ -58,7 +58,7 @@ typedef struct {
   int32_t restart;    /* m */
   int32_t fmt;        /* basis storage format */
   int32_t frsz2_bits; /* l in {16, 21, 32} when fmt == ORC_FRSZ2 */
-  int32_t pad_;
+  int32_t precond;    /* the M of Fig. 1 steps 3 and 17: 0 for M = I, 1 for M = diag(A) (Jacobi) */
   double tol;         /* target relative residual ||b - A x|| / ||b|| (Eq. 4) */
   int64_t max_iters;  /* cap on Arnoldi steps */
   double eta;         /* re-orthogonalization threshold of Fig. 1 step 7 */
@@ -74,7 +74,8 @@ typedef struct {
   double implicit_rrn; /* last |g_{j+1}| / ||b|| of the Givens recurrence */
 } orc_gmres_result;
 
-/* Solves A x = b. x holds x0 on entry and the result on exit. hist_implicit (may be NULL) gets
+/* Solves A x = b. x holds x0 on entry and the result on exit. Returns -3 when the Jacobi
+ * preconditioner meets a zero, non-finite or missing diagonal entry. hist_implicit (may be NULL) gets
  * the implicit RRN after every Arnoldi step (capacity max_iters); hist_true (may be NULL) gets
  * the explicit RRN at the start of every cycle (capacity max_iters + 2). Returns 0. */
 int orc_gmres(int32_t n, const int32_t* row_ptr, const int32_t* col, const double* vals,

@@ -17,6 +17,7 @@ from . import build as _build
 
 FP64, FP32, FP16, BF16, FRSZ2 = 0, 1, 2, 3, 4
 FORMATS = {"fp64": FP64, "fp32": FP32, "fp16": FP16, "bf16": BF16, "frsz2": FRSZ2}
+PRECOND = {"none": 0, "jacobi": 1}
 STATUS = {0: "CBG_OK", -1: "CBG_ERR_INVALID_ARG", -2: "CBG_ERR_CUDA", -3: "CBG_ERR_OOM", -4: "CBG_ERR_NONFINITE",
           -5: "CBG_ERR_NOT_CONVERGED", -6: "CBG_ERR_TIMEOUT", -7: "CBG_ERR_BAD_MATRIX", -8: "CBG_ERR_STATE"}
 ERR_NOT_CONVERGED = -5
@@ -40,7 +41,7 @@ class CbgError(RuntimeError):
 class Opts(ctypes.Structure):
     _fields_ = [("restart", ctypes.c_int32), ("fmt", ctypes.c_int32), ("frsz2_bits", ctypes.c_int32),
                 ("history", ctypes.c_int32), ("tol", ctypes.c_double), ("max_iters", ctypes.c_int64),
-                ("eta", ctypes.c_double)]
+                ("eta", ctypes.c_double), ("precond", ctypes.c_int32), ("reserved_", ctypes.c_int32)]
 
 
 class Result(ctypes.Structure):
@@ -293,6 +294,8 @@ def default_opts(**kw) -> Opts:
     for k, v in kw.items():
         if k == "fmt" and isinstance(v, str):
             v = FORMATS[v]
+        if k == "precond" and isinstance(v, str):
+            v = PRECOND[v]
         setattr(o, k, v)
     return o
 

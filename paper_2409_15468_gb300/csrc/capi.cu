@@ -230,7 +230,7 @@ int cbg_basis_store(const cbg_basis* basis, int32_t slot, const double* d_src, v
   DeviceInfo di;
   st = device_info(&di);
   if (st) return st;
-  return launch_store(mut(basis), slot, d_src, nullptr, nullptr, Gate{nullptr, nullptr},
+  return launch_store(mut(basis), slot, d_src, nullptr, nullptr, nullptr, Gate{nullptr, nullptr},
                       static_cast<cudaStream_t>(stream));
 }
 

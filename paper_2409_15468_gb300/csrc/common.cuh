@@ -19,6 +19,7 @@ enum DevErr : int {
   kDevErrTimeout = 1,     // a bounded mbarrier wait expired
   kDevErrNonFinite = 2,   // a norm became NaN or Inf
   kDevErrBadMatrix = 4,   // CSR validation failed
+  kDevErrBadDiagonal = 8, // a zero or missing diagonal entry (Jacobi preconditioner)
 };
 
 // A wait on a bulk copy gives up after this many nanoseconds of %globaltimer.

@@ -79,9 +79,11 @@ int launch_basis_update(const BasisView& B, int nvec, const int* nvec_dev, const
                         const Gate& gate, cudaStream_t stream);
 
 // ---- codec.cu -----------------------------------------------------------------------------------
-// Stores src (times *rcp when rcp is not null, also written to vout) into basis vector `slot`.
-int launch_store(const BasisMut& B, int slot, const double* src, const double* rcp, double* vout, const Gate& gate,
-                 cudaStream_t stream);
+// Stores src (times *rcp when rcp is not null) into basis vector `slot`; with rcp, the scaled
+// vector is also written to vout, multiplied elementwise by dscale when dscale is not null (the
+// SpMV input M^{-1} v of a right preconditioner M = diag^{-1}(dscale)).
+int launch_store(const BasisMut& B, int slot, const double* src, const double* rcp, double* vout,
+                 const double* dscale, const Gate& gate, cudaStream_t stream);
 int launch_frsz2_compress(const double* src, int64_t n, int l, uint32_t* exps, uint32_t* codes, cudaStream_t stream);
 int launch_frsz2_decompress(const uint32_t* exps, const uint32_t* codes, int64_t n, int l, double* dst,
                             cudaStream_t stream);
@@ -92,6 +94,10 @@ int launch_load(const BasisView& B, int slot, double* dst, cudaStream_t stream);
 int launch_spmv(int n, int64_t nnz, const int32_t* row_ptr, const int32_t* col, const double* vals, const double* x,
                 double* y, const double* bsub, double* partials, unsigned int* counter, int* err,
                 const NormEpilogue& epi, const Gate& gate, cudaStream_t stream);
+// dinv := 1 / diag(A) (kDevErrBadDiagonal on a zero or missing entry); x += d .* z.
+int launch_jacobi_diag(int n, const int32_t* row_ptr, const int32_t* col, const double* vals, double* dinv, int* err,
+                       cudaStream_t stream);
+int launch_add_scaled(int64_t n, const double* d, const double* z, double* x, cudaStream_t stream);
 int launch_validate_csr(int n, int64_t nnz, const int32_t* row_ptr, const int32_t* col, int* err,
                         cudaStream_t stream);
 int launch_sumsq(const double* x, int64_t n, double* partials, unsigned int* counter, int* err, double* out,

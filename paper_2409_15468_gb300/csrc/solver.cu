@@ -225,6 +225,7 @@ struct cbg_ctx {
   bool owns_pinned;
   BasisMut basis;
   double *v, *w, *H, *R, *cs, *sn, *g, *u, *y, *partials, *hist, *bnorm2;
+  double *dinv, *z;  // Jacobi preconditioner: 1 / diag(A) and the restart's V y (null without)
   SolverCtl* ctl;
   SolverCtl* ctl_host;  // pinned mirror
   double* bnorm2_host;  // pinned
@@ -247,7 +248,7 @@ namespace {
 struct Layout {
   int64_t vstride, estride;
   size_t off_basis_vals, off_basis_exps, off_v, off_w, off_H, off_R, off_cs, off_sn, off_g, off_u, off_y,
-      off_partials, off_hist, off_ctl, off_bnorm2, total;
+      off_partials, off_hist, off_ctl, off_bnorm2, off_dinv, off_z, total;
 };
 
 bool opts_valid(int32_t n, const cbg_opts* o) {
@@ -259,6 +260,8 @@ bool opts_valid(int32_t n, const cbg_opts* o) {
   if (!(o->eta >= 0.0) || !std::isfinite(o->eta)) return false;
   if (o->fmt < CBG_FP64 || o->fmt > CBG_FRSZ2) return false;
   if (o->fmt == CBG_FRSZ2 && o->frsz2_bits != 16 && o->frsz2_bits != 21 && o->frsz2_bits != 32) return false;
+  if (o->precond != CBG_PRECOND_NONE && o->precond != CBG_PRECOND_JACOBI) return false;
+  if (o->reserved_ != 0) return false;
   return true;
 }
 
@@ -287,6 +290,9 @@ Layout layout_of(int32_t n, const cbg_opts* o) {
   L.off_hist = take(o->history ? 8 * (o->max_iters + 1) : 0);
   L.off_ctl = take(sizeof(SolverCtl));
   L.off_bnorm2 = take(8);
+  const bool jac = o->precond == CBG_PRECOND_JACOBI;
+  L.off_dinv = take(jac ? 8ll * n : 0);
+  L.off_z = take(jac ? 8ll * n : 0);
   L.total = off;
   return L;
 }
@@ -367,7 +373,7 @@ int enqueue_step(cbg_ctx* c, int j) {
   st = launch_givens(givens_args(c), j, c->stream);
   if (st) return st;
   if (j + 1 <= c->opts.restart) {
-    st = launch_store(c->basis, j + 1, c->w, &ctl->rcp, c->v, run, c->stream);
+    st = launch_store(c->basis, j + 1, c->w, &ctl->rcp, c->v, c->dinv, run, c->stream);
     if (st) return st;
   }
   return CBG_OK;
@@ -381,8 +387,19 @@ int enqueue_restart(cbg_ctx* c) {
   int st = launch_backsub(a, c->y, c->stream);
   if (st) return st;
   NormEpilogue none{nullptr, nullptr, kEpiNone};
+  if (c->dinv) {
+    // x := x + M^{-1} (V y): z := V y (the update of a zero vector by -y), then x += dinv .* z
+    cudaError_t ez = cudaMemsetAsync(c->z, 0, sizeof(double) * c->n, c->stream);
+    if (ez != cudaSuccess) return cuda_fail(ez, "restart scratch clear");
+    st = launch_basis_update(B, c->opts.restart, &ctl->m_ls, c->y, 1, c->z, c->partials, &ctl->counters[kCtrUpdate],
+                             &ctl->err, none, Gate{nullptr, nullptr}, c->stream);
+    if (st) return st;
+    st = launch_add_scaled(c->n, c->dinv, c->z, c->x, c->stream);
+    if (st) return st;
+    return enqueue_residual(c);
+  }
   st = launch_basis_update(B, c->opts.restart, &ctl->m_ls, c->y, 1, c->x, c->partials, &ctl->counters[kCtrUpdate],
-                               &ctl->err, none, Gate{nullptr, nullptr}, c->stream);
+                           &ctl->err, none, Gate{nullptr, nullptr}, c->stream);
   if (st) return st;
   return enqueue_residual(c);
 }
@@ -398,6 +415,10 @@ int status_from_err(int err) {
   }
   if (err & kDevErrBadMatrix) {
     set_error("invalid CSR matrix");
+    return CBG_ERR_BAD_MATRIX;
+  }
+  if (err & kDevErrBadDiagonal) {
+    set_error("the Jacobi preconditioner needs a finite nonzero diagonal entry in every row");
     return CBG_ERR_BAD_MATRIX;
   }
   return CBG_OK;
@@ -437,7 +458,7 @@ int after_residual(cbg_ctx* c) {
   st = launch_cycle_init(c->ctl, c->g, c->opts.restart, c->steps_allowed, c->stream);
   if (st) return ctx_fail(c, st);
   // v_1 := r0 / beta, stored as basis vector 0 (step 1)
-  st = launch_store(c->basis, 0, c->w, &c->ctl->rcp, c->v, Gate{nullptr, nullptr}, c->stream);
+  st = launch_store(c->basis, 0, c->w, &c->ctl->rcp, c->v, c->dinv, Gate{nullptr, nullptr}, c->stream);
   if (st) return ctx_fail(c, st);
   c->j = 0;
   c->phase = kInCycle;
@@ -514,6 +535,9 @@ int ctx_create_in(cbg_ctx** out, int32_t n, int64_t nnz, const int32_t* d_row_pt
   c->hist = c->opts.history ? reinterpret_cast<double*>(base + L.off_hist) : nullptr;
   c->ctl = reinterpret_cast<SolverCtl*>(base + L.off_ctl);
   c->bnorm2 = reinterpret_cast<double*>(base + L.off_bnorm2);
+  const bool jac = c->opts.precond == CBG_PRECOND_JACOBI;
+  c->dinv = jac ? reinterpret_cast<double*>(base + L.off_dinv) : nullptr;
+  c->z = jac ? reinterpret_cast<double*>(base + L.off_z) : nullptr;
   c->ctl_host = static_cast<SolverCtl*>(pinned);
   c->bnorm2_host = reinterpret_cast<double*>(static_cast<uint8_t*>(pinned) + sizeof(SolverCtl) + 16);
   cudaError_t e = cudaEventCreateWithFlags(&c->ev, cudaEventDisableTiming);
@@ -585,6 +609,8 @@ int cbg_opts_default(cbg_opts* o) {
   o->tol = 1e-10;
   o->max_iters = 20000;
   o->eta = 0.70710678118654752440;
+  o->precond = CBG_PRECOND_NONE;
+  o->reserved_ = 0;
   return CBG_OK;
 }
 
@@ -675,6 +701,10 @@ int cbgmres_start(cbg_ctx* c, const double* d_b, double* d_x) {
   k_set_bnorm<<<1, 1, 0, c->stream>>>(c->ctl, c->bnorm2, c->opts.tol, c->opts.eta);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return ctx_fail(c, cuda_fail(e, "set bnorm launch"));
+  if (c->dinv) {  // M^{-1} = 1 / diag(A), after k_set_bnorm has cleared the error word
+    st = launch_jacobi_diag(c->n, c->row_ptr, c->col, c->vals, c->dinv, &c->ctl->err, c->stream);
+    if (st) return ctx_fail(c, st);
+  }
   e = cudaMemcpyAsync(c->bnorm2_host, c->bnorm2, 8, cudaMemcpyDeviceToHost, c->stream);
   if (e != cudaSuccess) return ctx_fail(c, cuda_fail(e, "bnorm copy"));
   st = enqueue_residual(c);

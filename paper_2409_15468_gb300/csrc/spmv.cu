@@ -139,6 +139,32 @@ __global__ void __launch_bounds__(256) k_spmv_vec(int n, const int32_t* __restri
   }
 }
 
+// dinv[i] = 1 / a_ii for the Jacobi preconditioner M = diag(A) (entries of row i in column i are
+// summed); a zero, non-finite or missing diagonal sets kDevErrBadDiagonal. Runs only on a
+// validated matrix.
+__global__ void k_jacobi_diag(int n, const int32_t* __restrict__ row_ptr, const int32_t* __restrict__ col,
+                              const double* __restrict__ vals, double* __restrict__ dinv, int* err) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+    double d = 0.0;
+    for (int p = row_ptr[i]; p < row_ptr[i + 1]; ++p)
+      if (col[p] == i) d += vals[p];
+    if (d == 0.0 || !isfinite(d)) {
+      atomicOr(err, kDevErrBadDiagonal);
+      dinv[i] = 0.0;
+    } else {
+      dinv[i] = 1.0 / d;
+    }
+  }
+}
+
+// x += d .* z (Fig. 1 step 17 with M^{-1} = diag(d): x_m := x_0 + M^{-1} (V_m y_m)).
+__global__ void k_add_scaled(int64_t n, const double* __restrict__ d, const double* __restrict__ z,
+                             double* __restrict__ x) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += stride) x[k] = fma(d[k], z[k], x[k]);
+}
+
 __global__ void k_validate_csr(int n, int64_t nnz, const int32_t* __restrict__ row_ptr,
                                const int32_t* __restrict__ col, int* err) {
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
@@ -215,6 +241,21 @@ int launch_spmv(int n, int64_t nnz, const int32_t* row_ptr, const int32_t* col, 
   }
   cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? CBG_OK : cuda_fail(e, "spmv launch");
+}
+
+int launch_jacobi_diag(int n, const int32_t* row_ptr, const int32_t* col, const double* vals, double* dinv, int* err,
+                       cudaStream_t stream) {
+  if (n <= 0) return CBG_OK;
+  k_jacobi_diag<<<grid_rows(n, 8), 256, 0, stream>>>(n, row_ptr, col, vals, dinv, err);
+  cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? CBG_OK : cuda_fail(e, "jacobi diagonal launch");
+}
+
+int launch_add_scaled(int64_t n, const double* d, const double* z, double* x, cudaStream_t stream) {
+  if (n <= 0) return CBG_OK;
+  k_add_scaled<<<grid_rows(n, 8), 256, 0, stream>>>(n, d, z, x);
+  cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? CBG_OK : cuda_fail(e, "scaled add launch");
 }
 
 int launch_validate_csr(int n, int64_t nnz, const int32_t* row_ptr, const int32_t* col, int* err,

@@ -21,7 +21,7 @@ def c1():
 @pytest.mark.parametrize("matrix", ["c1", "3d", "powerlaw", "powerlaw_short", "powerlaw_long"])
 def test_spmv(cbg, orc, matrix):
     # c1 and 3d take the thread-per-row kernel; the power-law matrices (mean row length ~15, ~29
-    # and ~58) take the lanes-per-row kernel with 8, 8 and 16 lanes
+    # and ~58) take the lanes-per-row kernel
     if matrix == "c1":
         A, _ = c1()
     elif matrix == "3d":
@@ -203,3 +203,36 @@ def test_basis_vector_orthonormal(cbg, fmt, l, bound):
             S2.basis_vector(21)
         finally:
             S2.close()
+
+
+@pytest.mark.parametrize("fmt,l", [("fp64", 32), ("frsz2", 32)])
+def test_gmres_jacobi_parity(cbg, orc, fmt, l):
+    """Right Jacobi preconditioning (Fig. 1 steps 3 and 17 with M = diag(A)) on a power-law matrix
+    whose row sums span orders of magnitude, against the oracle's preconditioned solve."""
+    A = workloads.powerlaw(3000, seed=3)
+    rp, col, vals = A.numpy()
+    b = orc.spmv(rp, col, vals, np.ones(A.n))
+    ref = orc.gmres(rp, col, vals, b, restart=30, tol=1e-10, fmt=orc.FORMAT_NAMES[fmt], l=l,
+                    precond="jacobi")
+    Ad = A.to("cuda")
+    S = cbg.Solver(Ad.row_ptr, Ad.col, Ad.vals, restart=30, tol=1e-10, fmt=fmt, frsz2_bits=l, precond="jacobi")
+    x = torch.zeros(A.n, dtype=torch.float64, device="cuda")
+    r = S.solve(torch.from_numpy(b).cuda(), x)
+    S.close()
+    assert ref.converged and r.converged and r.true_rrn <= 1e-10
+    assert abs(r.iters - ref.iters) <= max(1, 0.02 * ref.iters)
+    assert np.linalg.norm(x.cpu().numpy() - ref.x) / np.linalg.norm(ref.x) <= 1e-8
+    r0 = orc.gmres(rp, col, vals, b, restart=30, tol=1e-10, fmt=orc.FORMAT_NAMES[fmt], l=l)
+    assert ref.iters < r0.iters
+
+
+def test_jacobi_zero_diagonal_is_an_error(cbg):
+    """A row without a diagonal entry: the solve ends with CBG_ERR_BAD_MATRIX (no device fault)."""
+    rp = torch.tensor([0, 2, 3, 5], dtype=torch.int32, device="cuda")
+    col = torch.tensor([0, 2, 2, 0, 2], dtype=torch.int32, device="cuda")  # row 1 has no (1, 1)
+    vals = torch.tensor([4.0, 1.0, 3.0, 1.0, 5.0], dtype=torch.float64, device="cuda")
+    S = cbg.Solver(rp, col, vals, restart=3, precond="jacobi")
+    with pytest.raises(cbg.CbgError) as e:
+        S.solve(torch.ones(3, dtype=torch.float64, device="cuda"), torch.zeros(3, dtype=torch.float64, device="cuda"))
+    assert e.value.status == -7
+    S.close()

@@ -31,10 +31,17 @@ MUTATIONS = [
     ("rhs_rotation_sign", "ws->g[j + 1] = -s * ws->g[j];", "ws->g[j + 1] = s * ws->g[j];", "test_oracle_gmres.py"),
     ("backsub_transposed", "t -= ws->R[(size_t)i * ld + k] * ws->y[i];", "t -= ws->R[(size_t)k * ld + i] * ws->y[i];",
      "test_oracle_gmres.py"),
-    ("solution_update_dropped_vector", "for (int i = 0; i < mls; ++i) {\n    const double* vi",
-     "for (int i = 1; i < mls; ++i) {\n    const double* vi", "test_oracle_gmres.py"),
-    ("spmv_dropped_last_entry", "for (int32_t p = row_ptr[i]; p < row_ptr[i + 1]; ++p)",
-     "for (int32_t p = row_ptr[i]; p + 1 < row_ptr[i + 1]; ++p)", "test_oracle_gmres.py"),
+    ("solution_update_dropped_vector",
+     "for (int i = 0; i < mls; ++i) {\n      const double* vi = ws->vhat + (size_t)i * n;\n      for (int32_t k = 0; k < n; ++k) x[k]",
+     "for (int i = 1; i < mls; ++i) {\n      const double* vi = ws->vhat + (size_t)i * n;\n      for (int32_t k = 0; k < n; ++k) x[k]",
+     "test_oracle_gmres.py"),
+    ("spmv_dropped_last_entry", "for (int32_t p = row_ptr[i]; p < row_ptr[i + 1]; ++p) s +=",
+     "for (int32_t p = row_ptr[i]; p + 1 < row_ptr[i + 1]; ++p) s +=", "test_oracle_gmres.py"),
+    ("jacobi_step3_unpreconditioned", "orc_spmv_csr(n, ws->row_ptr, ws->col, ws->vals, ws->t, ws->w);",
+     "orc_spmv_csr(n, ws->row_ptr, ws->col, ws->vals, ws->v, ws->w);", "test_oracle_gmres.py"),
+    ("jacobi_step17_unscaled", "for (int32_t k = 0; k < n; ++k) x[k] += ws->dinv[k] * ws->t[k];",
+     "for (int32_t k = 0; k < n; ++k) x[k] += ws->t[k];", "test_oracle_gmres.py"),
+    ("jacobi_m_not_inverted", "ws->dinv[i] = 1.0 / d;", "ws->dinv[i] = d;", "test_oracle_gmres.py"),
 ]
 
 
