@@ -399,6 +399,33 @@ def sweep(pkg, torch, device, matrix: str = "c3", rhs: str = "ones", formats=Non
     return out
 
 
+def spmv_only(pkg, torch, device, kind: str, size: int, runs: int = 10):
+    """The SpMV alone: c3 = 3D convection-diffusion on a size^3 grid, c4 = power-law matrix with
+    `size` rows; the minimum of `runs` CUDA-event timings, algorithmic bytes 12 nnz + 20 n."""
+    import workloads
+
+    if kind == "c4":
+        A = workloads.powerlaw(size, seed=2, device=device)
+    else:
+        A = workloads.convdiff(size, 3, (1.0, 1.0, 1.0), 50.0, device=device)
+    x = torch.ones(A.n, dtype=torch.float64, device=device)
+    y = torch.empty_like(x)
+    nrm = torch.empty(1, dtype=torch.float64, device=device)
+    for _ in range(2):
+        pkg.spmv(A.row_ptr, A.col, A.vals, x, y=y, norm2=nrm)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    best = float("inf")
+    for _ in range(runs):
+        e0.record()
+        pkg.spmv(A.row_ptr, A.col, A.vals, x, y=y, norm2=nrm)
+        e1.record()
+        torch.cuda.synchronize()
+        best = min(best, e0.elapsed_time(e1))
+    byt = 12 * A.nnz + 4 * (A.n + 1) + 16 * A.n
+    return {"matrix": kind, "n": A.n, "nnz": A.nnz, "ms": best, "gbs": byt / (best * 1e-3) / 1e9,
+            "algorithmic_bytes": byt}
+
+
 INTENSITY_R = [0, 1, 2, 3, 4, 5, 6, 7, 8, 10, 12, 14, 16, 20, 24, 28, 32, 40, 48, 56, 64, 80, 96, 112, 128, 192, 256]
 
 
@@ -580,6 +607,17 @@ def cpu_baseline(n_full: int, nvec: int):
 
 # ------------------------------------------------------------------------------------------------
 
+def max_over_ranks(dist, value: float, device) -> float:
+    """The maximum of a per-rank time over all ranks (the job takes as long as its slowest rank)."""
+    if dist is None:
+        return value
+    import torch
+
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
     ap.add_argument("--gpus", type=int, default=1)
@@ -599,6 +637,10 @@ def main():
     ap.add_argument("--sweep", default="", choices=["", "c3", "c4"],
                     help="run only the basis-format sweep (iteration ratios, RRN histories, exponent spreads)")
     ap.add_argument("--rhs", default="ones", choices=["ones", "sin"], help="right-hand side of --sweep")
+    ap.add_argument("--ref-budget", type=float, default=150.0,
+                    help="seconds of host time the reference (oracle) arm's steps may take in total")
+    ap.add_argument("--spmv", default="", choices=["", "c3", "c4"], help="run only the SpMV on a c3/c4 matrix")
+    ap.add_argument("--spmv-size", type=int, default=256, help="--spmv c3: grid edge; c4: rows")
     ap.add_argument("--intensity", action="store_true",
                     help="run only the arithmetic-intensity sweep of the stored formats (Fig. 3 protocol)")
     ap.add_argument("--target-iters", type=int, default=0,
@@ -617,8 +659,7 @@ def main():
     if args.impl == "reference":
         if rank != 0:
             return
-        budget = 150.0
-        n = choose_oracle_sample(args.nvec, args.steps + args.warmup, budget, args.n)
+        n = choose_oracle_sample(args.nvec, args.steps + args.warmup, args.ref_budget, args.n)
         gbs, dt = oracle_rate(n, args.nvec, args.steps, args.warmup)
         line = {"impl": "reference", "metric": METRIC, "value": gbs, "unit": "GB/s", "n_gpus": args.gpus,
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3 / args.steps,
@@ -645,6 +686,13 @@ def main():
     device = torch.device("cuda", local if world > 1 else torch.cuda.current_device())
     torch.cuda.set_device(device)
     peak, peak_src = load_peaks()
+    if args.spmv:
+        if rank == 0:
+            print(json.dumps({"spmv": spmv_only(pkg, torch, device, args.spmv, args.spmv_size)}))
+        if dist:
+            dist.barrier()
+            dist.destroy_process_group()
+        return
     if args.intensity:
         if rank == 0:
             print(json.dumps({"intensity": intensity_sweep(pkg, torch, device, peak_gbs=peak)}))
@@ -681,13 +729,18 @@ def main():
     sampler = ClockSampler(device.index if device.index is not None else 0).start() if rank == 0 else None
     time.sleep(0.3)
     total_ms, _ = time_steps(pkg, torch, B, w, args.nvec, args.steps, args.warmup)
-    if dist:
-        t = torch.tensor([total_ms], device=device)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = max_over_ranks(dist, total_ms, device)
     # per-kernel durations for the roofline (a separate pass, same launches)
     _, kms = time_steps(pkg, torch, B, w, args.nvec, max(20, min(args.steps, 100)), 2, per_kernel=True)
     clocks = sampler.stop() if sampler else None
+    # end to end through host buffers, on every rank (max over ranks, like the device time)
+    e_steps = max(20, args.steps // 5)
+    e2e = None
+    if not args.no_extras:
+        e_ms, h2d, d2h = time_e2e(pkg, torch, B, w, args.nvec, e_steps, 3)
+        e_ms = max_over_ranks(dist, e_ms, device)
+        e2e = {"value": world * per_step * e_steps / (e_ms * 1e-3) / 1e9, "unit": "GB/s", "h2d_bytes_per_step": h2d,
+               "d2h_bytes_per_step": d2h, "steps": e_steps}
     if rank != 0:
         dist.barrier()
         dist.destroy_process_group()
@@ -710,12 +763,10 @@ def main():
                        "parallelism": f"replicas x{world}" if world > 1 else "1 GPU"},
             "roofline": roofline, "gpu_launches": 3 * args.steps, "clocks": clocks}
 
-    if not args.no_extras:
-        # e2e through host buffers
-        e_ms, h2d, d2h = time_e2e(pkg, torch, B, w, args.nvec, max(20, args.steps // 5), 3)
-        e_steps = max(20, args.steps // 5)
-        line["e2e"] = {"value": per_step * e_steps / (e_ms * 1e-3) / 1e9, "unit": "GB/s", "h2d_bytes_per_step": h2d,
-                       "d2h_bytes_per_step": d2h, "steps": e_steps}
+    if e2e:
+        line["e2e"] = e2e
+    if not args.no_extras and world == 1:
+        # the single-GPU legs (other formats, full solves, serving, the oracle on the host) run at N = 1
         del B, w
         torch.cuda.empty_cache()
         # the other storage formats on the same step
