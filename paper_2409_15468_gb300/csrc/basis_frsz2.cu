@@ -330,9 +330,9 @@ struct FUpd {
   static constexpr int kVps = 4;  // basis vectors per stage
   static constexpr int kStages = S;
   static constexpr int kGroup = 32;
-  // resident CTAs per SM the register allocation is capped for (l < 32 is faster with a few spills
-  // and one more CTA); the deep pipeline runs one CTA per SM
-  static constexpr int kMinBlocks = S == 12 ? 1 : (L == 32 ? 5 : 6);
+  // resident CTAs per SM the register allocation is capped for (measured per code width: l = 16
+  // is fastest with a few spills at 6, l = 21 with 4); the deep pipeline runs one CTA per SM
+  static constexpr int kMinBlocks = S == 12 ? 1 : (L == 32 ? 5 : (L == 21 ? 4 : 6));
   static constexpr int kVecBytes = kBlocks * L * 4;
   static constexpr int kStageBytes = kVps * kVecBytes;
   // dynamic smem: stages | coefficient table [kGroup][kBlocks] (int2) | exponent words of one group

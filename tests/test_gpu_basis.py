@@ -129,3 +129,26 @@ def test_intensity(cbg, orc, fmt, l, r):
         ref32 = orc.dot2(y32.astype(np.float64), np.ones(n))
         got32 = B.intensity(1, r, fp32_compute=True).item()
         assert abs(got32 - ref32) <= 8 * 2.0 ** -24 * np.abs(y32.astype(np.float64)).sum()
+
+
+@pytest.mark.parametrize("l", [16, 21, 32])
+@pytest.mark.parametrize("nvec", [33, 300, 1025])
+def test_update_many_groups(cbg, orc, l, nvec):
+    """The FRSZ2 update combines groups of 32 vectors in integers at rescaled block scales: many
+    groups (2^gb >= ceil(nvec/32) sets the rounding unit) and the largest restart the solver takes
+    (1024, plus one)."""
+    n = 2048 + 77
+    B, Vhat, exps = make_basis(cbg, orc, n, nvec, 4, l, seed=nvec + l)
+    rng = np.random.default_rng(nvec)
+    w = rng.standard_normal(n)
+    h = rng.standard_normal(nvec) * np.exp2(rng.integers(-30, 3, nvec))
+    wd = torch.from_numpy(w).cuda()
+    B.update(nvec, torch.from_numpy(h).cuda(), wd)
+    out = wd.cpu().numpy()
+    ref = orc.basis_update(Vhat, h, w)
+    terms = np.abs(Vhat * h[:, None])
+    e = np.maximum(exps[:, np.arange(n) // 32].astype(np.float64), 1.0)
+    tmax = (np.abs(h)[:, None] * np.exp2(e - 1023.0 + 1.0)).max(axis=0)
+    tol = 4 * (2.0 ** -50 * (np.abs(w) + terms.sum(axis=0)) + nvec * 2.0 ** -53 * tmax) + 1e-300
+    err = np.abs(out - ref)
+    assert np.all(err <= tol), (err / tol).max()
