@@ -27,19 +27,22 @@
 namespace cbg {
 
 // ================================================================================================
-// dot: one thread per 32-value block, 128 blocks per tile; CTA (x, y) takes block range x and the
-// y-th slice of the vectors (gridDim.y > 1 only when the blocks alone leave the GPU underfilled)
+// dot: one thread per 32-value block, 128 blocks per tile, two basis vectors per pipeline stage;
+// CTA (x, y) takes block range x and the y-th slice of the vectors (gridDim.y > 1 only when the
+// blocks alone leave the GPU underfilled)
 // ================================================================================================
 
 template <int L>
 struct FDot {
   static constexpr int kThreads = 128;
   static constexpr int kWarps = 4;
-  static constexpr int kStages = (L == 32) ? 3 : 4;
-  static constexpr int kBatch = 8;       // vectors per per-warp reduction
+  static constexpr int kVps = 2;        // basis vectors per pipeline stage
+  static constexpr int kStages = 2;
+  static constexpr int kBatch = 4;       // vectors per per-warp reduction
   static constexpr int kRedStride = 33;  // doubles per batch row (padded against bank conflicts)
   static constexpr int kCodeBytes = kThreads * L * 4;
-  static constexpr int kStageBytes = kCodeBytes + kThreads * 4;
+  static constexpr int kVecBytes = kCodeBytes + kThreads * 4;  // one vector's codes and exponents
+  static constexpr int kStageBytes = kVps * kVecBytes;
   static constexpr int kRedDoubles = kWarps * kBatch * kRedStride;
   static size_t smem_bytes(int nvec) {
     return (size_t)kStages * kStageBytes + (size_t)kRedDoubles * 8 + (size_t)kWarps * nvec * 8 +
@@ -144,7 +147,9 @@ __global__ void __launch_bounds__(FDot<L>::kThreads) k_dot_frsz2(BasisView B, in
   // this CTA's vectors [v_lo, v_lo + nv)
   const int v_lo = static_cast<int>((int64_t)nvec * blockIdx.y / gridDim.y);
   const int nv = static_cast<int>((int64_t)nvec * (blockIdx.y + 1) / gridDim.y) - v_lo;
-  const int total = ntiles * nv;
+  constexpr int VPS = C::kVps;
+  const int units = (nv + VPS - 1) / VPS;  // stages per tile
+  const int total = ntiles * units;
   const int cid = blockIdx.y * gridDim.x + blockIdx.x, nctas = gridDim.x * gridDim.y;
 
   for (int i = t; i < C::kWarps * nvec; i += T) hpart[i] = 0.0;
@@ -158,18 +163,22 @@ __global__ void __launch_bounds__(FDot<L>::kThreads) k_dot_frsz2(BasisView B, in
   }
   __syncthreads();
 
-  auto issue = [&](int p) {
-    const int tile = p / nv, vec = v_lo + (p - tile * nv), s = p % S;
+  auto issue = [&](int p) {  // stage unit p: vectors v_lo + VPS u .. of tile p / units
+    const int tile = p / units, u = p - tile * units, s = p % S;
+    const int v0 = v_lo + u * VPS, cnt = min(VPS, v_lo + nv - v0);
     const int64_t tb0 = b0 + (int64_t)tile * T;
     const int nbt = static_cast<int>(min((int64_t)T, b1 - tb0));
     const uint32_t cbytes = static_cast<uint32_t>((nbt * L * 4 + 15) & ~15);
     const uint32_t ebytes = static_cast<uint32_t>((nbt * 4 + 15) & ~15);
-    uint8_t* dst = stages + s * C::kStageBytes;
     fence_proxy_async_smem();
-    mbar_arrive_expect_tx(&full[s], cbytes + ebytes);
-    bulk_g2s(dst, B.vals + (int64_t)vec * B.vstride + tb0 * L * 4, cbytes, &full[s]);
-    bulk_g2s(dst + C::kCodeBytes, reinterpret_cast<const uint8_t*>(B.exps) + (int64_t)vec * B.estride + tb0 * 4,
-             ebytes, &full[s]);
+    mbar_arrive_expect_tx(&full[s], (cbytes + ebytes) * cnt);
+    for (int j = 0; j < cnt; ++j) {
+      uint8_t* dst = stages + s * C::kStageBytes + j * C::kVecBytes;
+      const int vec = v0 + j;
+      bulk_g2s(dst, B.vals + (int64_t)vec * B.vstride + tb0 * L * 4, cbytes, &full[s]);
+      bulk_g2s(dst + C::kCodeBytes, reinterpret_cast<const uint8_t*>(B.exps) + (int64_t)vec * B.estride + tb0 * 4,
+               ebytes, &full[s]);
+    }
   };
   int issued = 0;  // thread 0 only
   if (t == 0) {
@@ -226,7 +235,7 @@ __global__ void __launch_bounds__(FDot<L>::kThreads) k_dot_frsz2(BasisView B, in
 #pragma unroll
       for (int r = 0; r < 32; ++r) W1[r] = W0[r] = 0;
     }
-    for (int vi = 0; vi < nv; ++vi) {
+    for (int vi = 0; vi < nv; vi += VPS) {
       // lagged refill: the stage released by every warp in the previous iteration
       if (t == 0 && !first && issued < total && !rfail && !dead) {
         if (mbar_wait_bounded(&empty[ps], pph)) {
@@ -249,20 +258,42 @@ __global__ void __launch_bounds__(FDot<L>::kThreads) k_dot_frsz2(BasisView B, in
           }
         }
       }
-      double hp = 0.0;
-      if (active && ok) {
-        const uint8_t* st = stages + s * C::kStageBytes;
-        const uint32_t e = reinterpret_cast<const uint32_t*>(st + C::kCodeBytes)[t];
-        long long a1, a0;
-        block_dot<L>(reinterpret_cast<const uint32_t*>(st) + t * L, t, W1, W0, a1, a0);
-        // sum = (a1 2^27 + a0) 2^x with x = Ebar + Ew - 2096 - l, |a1 2^27 + a0| < 2^(l+57).
-        // Rounded to 2^(l-5) units it fits in 63 bits; the rounding error, at most 2^(l-6) units,
-        // is a quarter of the bound 2^-54 max|w| sum|vhat| of a block whose maxima are normal.
-        const long long th = (a1 << (32 - L)) + ((a0 + (1ll << (L - 6))) >> (L - 5));
-        const int x = (e > 1 ? static_cast<int>(e) : 1) + ew - 2096 - L;
-        hp = scale_pow2(static_cast<double>(th), x + L - 5);
+#pragma unroll
+      for (int j = 0; j < VPS; ++j) {
+        const int vj = vi + j;
+        if (vj >= nv) break;  // uniform
+        double hp = 0.0;
+        if (active && ok) {
+          const uint8_t* st = stages + s * C::kStageBytes + j * C::kVecBytes;
+          const uint32_t e = reinterpret_cast<const uint32_t*>(st + C::kCodeBytes)[t];
+          long long a1, a0;
+          block_dot<L>(reinterpret_cast<const uint32_t*>(st) + t * L, t, W1, W0, a1, a0);
+          // sum = (a1 2^27 + a0) 2^x with x = Ebar + Ew - 2096 - l, |a1 2^27 + a0| < 2^(l+57).
+          // Rounded to 2^(l-5) units it fits in 63 bits; the rounding error, at most 2^(l-6) units,
+          // is a quarter of the bound 2^-54 max|w| sum|vhat| of a block whose maxima are normal.
+          const long long th = (a1 << (32 - L)) + ((a0 + (1ll << (L - 6))) >> (L - 5));
+          const int x = (e > 1 ? static_cast<int>(e) : 1) + ew - 2096 - L;
+          hp = scale_pow2(static_cast<double>(th), x + L - 5);
+        }
+        myred[(vj % C::kBatch) * C::kRedStride + lane] = hp;
+        if (vj % C::kBatch == C::kBatch - 1 || vj == nv - 1) {
+          // row r of the batch holds vector first_v + r; lane (v, part) sums kBatch entries of
+          // row v, then the parts combine with shuffles
+          constexpr int KB = C::kBatch;
+          __syncwarp();
+          const int first_i = vj - (vj % KB), cnt = vj - first_i + 1, first_v = v_lo + first_i;
+          const int v = lane % KB, part = lane / KB;
+          double sacc = 0.0;
+          if (v < cnt) {
+#pragma unroll
+            for (int i = 0; i < KB; ++i) sacc += myred[v * C::kRedStride + part * KB + i];
+          }
+#pragma unroll
+          for (int o = KB; o < 32; o <<= 1) sacc += __shfl_xor_sync(0xffffffffu, sacc, o);
+          if (part == 0 && v < cnt) myh[first_v + v] += sacc;
+          __syncwarp();
+        }
       }
-      myred[(vi % C::kBatch) * C::kRedStride + lane] = hp;
       __syncwarp();
       if (lane == 0 && ok) mbar_arrive(&empty[s]);
       ps = s;
@@ -271,19 +302,6 @@ __global__ void __launch_bounds__(FDot<L>::kThreads) k_dot_frsz2(BasisView B, in
       if (++s == S) {
         s = 0;
         ph ^= 1u;
-      }
-      if (vi % C::kBatch == C::kBatch - 1 || vi == nv - 1) {
-        const int first_i = vi - (vi % C::kBatch), cnt = vi - first_i + 1, first_v = v_lo + first_i;
-        const int v = lane & 7, part = lane >> 3;
-        double sacc = 0.0;
-        if (v < cnt) {
-#pragma unroll
-          for (int i = 0; i < 8; ++i) sacc += myred[v * C::kRedStride + part * 8 + i];
-        }
-        sacc += __shfl_xor_sync(0xffffffffu, sacc, 8);
-        sacc += __shfl_xor_sync(0xffffffffu, sacc, 16);
-        if (part == 0 && v < cnt) myh[first_v + v] += sacc;
-        __syncwarp();
       }
     }
   }
