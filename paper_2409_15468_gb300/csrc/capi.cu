@@ -361,7 +361,7 @@ int cbg_spmv(int32_t n, int64_t nnz, const int32_t* d_row_ptr, const int32_t* d_
   st = take_work(d_work, work_bytes, 1, s, &w);
   if (st) return st;
   NormEpilogue epi{d_norm2, nullptr, kEpiNone};
-  return launch_spmv(n, nnz, d_row_ptr, d_col, d_vals, d_x, d_y, nullptr, w.partials, w.counter, w.err, epi,
+  return launch_spmv(n, nnz, d_row_ptr, d_col, d_vals, d_x, d_y, nullptr, nullptr, w.partials, w.counter, w.err, epi,
                      Gate{nullptr, nullptr}, s);
 }
 

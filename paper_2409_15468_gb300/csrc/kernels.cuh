@@ -92,8 +92,14 @@ int launch_load(const BasisView& B, int slot, double* dst, cudaStream_t stream);
 // ---- spmv.cu ------------------------------------------------------------------------------------
 // y = A x (or y = bsub - A x when bsub is not null); ||y||^2 to the epilogue. partials: kMaxGrid.
 int launch_spmv(int n, int64_t nnz, const int32_t* row_ptr, const int32_t* col, const double* vals, const double* x,
-                double* y, const double* bsub, double* partials, unsigned int* counter, int* err,
+                double* y, const double* bsub, const int32_t* perm, double* partials, unsigned int* counter, int* err,
                 const NormEpilogue& epi, const Gate& gate, cudaStream_t stream);
+// Lanes per row of the SpMV for this matrix shape (1: one thread per row, which ignores perm).
+int spmv_lanes_per_row(int n, int64_t nnz);
+// perm := the rows in a stable order by length bucket (see spmv.cu); scratch holds
+// row_order_scratch_bytes(n) bytes.
+size_t row_order_scratch_bytes(int n);
+int launch_row_order(int n, const int32_t* row_ptr, int32_t* perm, int32_t* scratch, cudaStream_t stream);
 // dinv := 1 / diag(A) (kDevErrBadDiagonal on a zero or missing entry); x += d .* z.
 int launch_jacobi_diag(int n, const int32_t* row_ptr, const int32_t* col, const double* vals, double* dinv, int* err,
                        cudaStream_t stream);

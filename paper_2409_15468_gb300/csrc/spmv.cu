@@ -69,13 +69,17 @@ template <int G, int U>
 __global__ void __launch_bounds__(256) k_spmv_vec(int n, const int32_t* __restrict__ row_ptr,
                                                   const int32_t* __restrict__ col, const double* __restrict__ vals,
                                                   const double* __restrict__ x, double* __restrict__ y,
-                                                  const double* __restrict__ bsub, double* __restrict__ partials,
-                                                  unsigned int* counter, int* err, NormEpilogue epi, Gate gate) {
+                                                  const double* __restrict__ bsub, const int32_t* __restrict__ perm,
+                                                  double* __restrict__ partials, unsigned int* counter, int* err,
+                                                  NormEpilogue epi, Gate gate) {
   if (gate_skip_s(gate)) return;
   __shared__ double red[8];
   __shared__ int flag;
   const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
   const int sub = lane & (G - 1);
+  // position j of the row order holds row perm[j] (rows sorted by length bucket, so the rows a
+  // warp handles together have similar lengths), or row j without a permutation
+  auto row_at = [&](int64_t j) -> int64_t { return perm ? static_cast<int64_t>(__ldg(perm + j)) : j; };
   double nrm = 0.0;
   const int64_t groups = (int64_t)gridDim.x * (blockDim.x / G);
   const int64_t g0 = (int64_t)blockIdx.x * (blockDim.x / G) + t / G;
@@ -83,13 +87,14 @@ __global__ void __launch_bounds__(256) k_spmv_vec(int n, const int32_t* __restri
   // shuffles below always see the whole warp
   const int64_t rows_per_group = ((int64_t)n + groups - 1) / groups;
   int p0 = 0, p1 = 0;
+  int64_t i = g0 < n ? row_at(g0) : n;
   if (g0 < n) {
-    p0 = __ldg(row_ptr + g0);
-    p1 = __ldg(row_ptr + g0 + 1);
+    p0 = __ldg(row_ptr + i);
+    p1 = __ldg(row_ptr + i + 1);
   }
   for (int64_t k = 0; k < rows_per_group; ++k) {
-    const int64_t i = g0 + k * groups;
-    const int64_t inext = i + groups;
+    const int64_t jnext = g0 + (k + 1) * groups;
+    const int64_t inext = jnext < n ? row_at(jnext) : n;
     int q0 = 0, q1 = 0;
     if (inext < n) {
       q0 = __ldg(row_ptr + inext);
@@ -120,6 +125,7 @@ __global__ void __launch_bounds__(256) k_spmv_vec(int n, const int32_t* __restri
     }
     p0 = q0;
     p1 = q1;
+    i = inext;
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) nrm += __shfl_xor_sync(0xffffffffu, nrm, o);
@@ -136,6 +142,80 @@ __global__ void __launch_bounds__(256) k_spmv_vec(int n, const int32_t* __restri
       if (lane == 0) norm_epilogue(epi, s, err);
     }
     if (t == 0) *counter = 0;
+  }
+}
+
+// ---- row order by length (for the lanes-per-row kernel) ----------------------------------------
+// A stable counting sort of the rows by the bucket floor(log2(len)) + 1 (capped at 11), in three
+// deterministic passes: counts per 256-row chunk, a per-bucket scan, and the scatter with ranks
+// from warp ballots. Rows that a warp then processes together have similar lengths, so a warp
+// does not iterate to the length of one long row while its other lanes idle.
+constexpr int kRowBuckets = 12;
+constexpr int kRowChunk = 256;
+
+__device__ __forceinline__ int row_bucket(const int32_t* row_ptr, int64_t i) {
+  const int len = row_ptr[i + 1] - row_ptr[i];
+  const int b = len > 0 ? 32 - __clz(len) : 0;
+  return b < kRowBuckets - 1 ? b : kRowBuckets - 1;
+}
+
+__global__ void __launch_bounds__(kRowChunk) k_row_count(int n, const int32_t* __restrict__ row_ptr,
+                                                         int32_t* __restrict__ counts) {
+  __shared__ int cnt[kRowBuckets];
+  const int t = threadIdx.x;
+  if (t < kRowBuckets) cnt[t] = 0;
+  __syncthreads();
+  const int64_t i = (int64_t)blockIdx.x * kRowChunk + t;
+  if (i < n) atomicAdd(&cnt[row_bucket(row_ptr, i)], 1);
+  __syncthreads();
+  if (t < kRowBuckets) counts[(int64_t)blockIdx.x * kRowBuckets + t] = cnt[t];
+}
+
+// One CTA, one warp per bucket: counts[c][b] becomes the position of chunk c's first row of
+// bucket b in the row order (buckets in increasing order, chunks in order within a bucket).
+__global__ void __launch_bounds__(32 * kRowBuckets) k_row_scan(int nchunks, int32_t* __restrict__ counts) {
+  __shared__ int total[kRowBuckets];
+  const int b = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  int carry = 0;
+  for (int c0 = 0; c0 < nchunks; c0 += 32) {
+    const int c = c0 + lane;
+    const int v = c < nchunks ? counts[(int64_t)c * kRowBuckets + b] : 0;
+    int incl = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int u = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += u;
+    }
+    if (c < nchunks) counts[(int64_t)c * kRowBuckets + b] = carry + incl - v;
+    carry += __shfl_sync(0xffffffffu, incl, 31);
+  }
+  if (lane == 0) total[b] = carry;
+  __syncthreads();
+  int base = 0;
+  for (int bb = 0; bb < b; ++bb) base += total[bb];
+  for (int c = lane; c < nchunks; c += 32) counts[(int64_t)c * kRowBuckets + b] += base;
+}
+
+__global__ void __launch_bounds__(kRowChunk) k_row_scatter(int n, const int32_t* __restrict__ row_ptr,
+                                                           const int32_t* __restrict__ offs,
+                                                           int32_t* __restrict__ perm) {
+  constexpr int W = kRowChunk / 32;
+  __shared__ int wcnt[W][kRowBuckets];
+  const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+  const int64_t i = (int64_t)blockIdx.x * kRowChunk + t;
+  const bool valid = i < n;
+  const int b = valid ? row_bucket(row_ptr, i) : -1;
+  int rank = 0;
+  for (int bb = 0; bb < kRowBuckets; ++bb) {
+    const unsigned m = __ballot_sync(0xffffffffu, b == bb);
+    if (lane == 0) wcnt[warp][bb] = __popc(m);
+    if (b == bb) rank = __popc(m & ((1u << lane) - 1u));
+  }
+  __syncthreads();
+  if (valid) {
+    int before = 0;
+    for (int w = 0; w < warp; ++w) before += wcnt[w][b];
+    perm[offs[(int64_t)blockIdx.x * kRowBuckets + b] + before + rank] = static_cast<int32_t>(i);
   }
 }
 
@@ -227,8 +307,20 @@ int spmv_lanes_per_row(int n, int64_t nnz) {
   return mean < 12.0 ? 1 : 4;
 }
 
+size_t row_order_scratch_bytes(int n) { return (size_t)((n + kRowChunk - 1) / kRowChunk) * kRowBuckets * 4; }
+
+int launch_row_order(int n, const int32_t* row_ptr, int32_t* perm, int32_t* scratch, cudaStream_t stream) {
+  if (n <= 0) return CBG_OK;
+  const int nchunks = (n + kRowChunk - 1) / kRowChunk;
+  k_row_count<<<nchunks, kRowChunk, 0, stream>>>(n, row_ptr, scratch);
+  k_row_scan<<<1, 32 * kRowBuckets, 0, stream>>>(nchunks, scratch);
+  k_row_scatter<<<nchunks, kRowChunk, 0, stream>>>(n, row_ptr, scratch, perm);
+  cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? CBG_OK : cuda_fail(e, "row order launch");
+}
+
 int launch_spmv(int n, int64_t nnz, const int32_t* row_ptr, const int32_t* col, const double* vals, const double* x,
-                double* y, const double* bsub, double* partials, unsigned int* counter, int* err,
+                double* y, const double* bsub, const int32_t* perm, double* partials, unsigned int* counter, int* err,
                 const NormEpilogue& epi, const Gate& gate, cudaStream_t stream) {
   if (n <= 0) return CBG_OK;
   const int g = spmv_lanes_per_row(n, nnz);
@@ -237,7 +329,8 @@ int launch_spmv(int n, int64_t nnz, const int32_t* row_ptr, const int32_t* col, 
     k_spmv<<<grid, 256, 0, stream>>>(n, row_ptr, col, vals, x, y, bsub, partials, counter, err, epi, gate);
   } else {
     const int grid = grid_rows((int64_t)n * g, 8);
-    k_spmv_vec<4, 8><<<grid, 256, 0, stream>>>(n, row_ptr, col, vals, x, y, bsub, partials, counter, err, epi, gate);
+    k_spmv_vec<4, 8><<<grid, 256, 0, stream>>>(n, row_ptr, col, vals, x, y, bsub, perm, partials, counter, err, epi,
+                                               gate);
   }
   cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? CBG_OK : cuda_fail(e, "spmv launch");
