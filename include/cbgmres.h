@@ -242,7 +242,8 @@ int cbgmres_finish(cbg_ctx* ctx, cbg_result* result);
  * the other requests in flight.
  *
  * Nothing in a turn waits on the device, allocates or frees device memory, or synchronises
- * the device. The matrix, b and x of a request are caller-owned device memory that must stay
+ * the device. A server is not thread-safe: call it from one thread at a time, with the device it
+ * was created on current. The matrix, b and x of a request are caller-owned device memory that must stay
  * valid until its completion is returned; x holds x0 on entry and the solution on completion. */
 typedef struct cbg_server cbg_server;
 

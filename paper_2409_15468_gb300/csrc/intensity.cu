@@ -16,7 +16,7 @@ namespace cbg {
 namespace {
 
 template <int F, int L>
-__device__ __forceinline__ double decode_at(const BasisView& B, const uint8_t* vals, const uint32_t* exps, int64_t k) {
+__device__ __forceinline__ double decode_at(const uint8_t* vals, const uint32_t* exps, int64_t k) {
   if (F == CBG_FRSZ2) return frsz2_decode<L>(exps, reinterpret_cast<const uint32_t*>(vals), k);
   if (F == CBG_FP64) return __ldcs(reinterpret_cast<const double*>(vals) + k);
   if (F == CBG_FP32) return widen_f32(__ldcs(reinterpret_cast<const uint32_t*>(vals) + k));
@@ -60,7 +60,7 @@ __global__ void __launch_bounds__(256) k_intensity(BasisView B, const uint8_t* _
 #pragma unroll
       for (int u = 0; u < 4; ++u) {
         const int64_t k = k0 + u * stride;
-        y[u] = k < n ? decode_at<F, L>(B, vals, exps, k) : 0.0;
+        y[u] = k < n ? decode_at<F, L>(vals, exps, k) : 0.0;
       }
       for (int s = 0; s < r; ++s) {
 #pragma unroll
