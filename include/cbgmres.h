@@ -35,7 +35,9 @@ extern "C" {
 #define CBG_ERR_NONFINITE (-4)    /* a norm or residual became NaN or infinite during a solve */
 #define CBG_ERR_NOT_CONVERGED (-5) /* max_iters reached; x and the result are still written */
 #define CBG_ERR_TIMEOUT (-6)      /* a bounded device-side wait expired; the context is unusable */
-#define CBG_ERR_BAD_MATRIX (-7)   /* CSR row pointers not monotone or a column index out of range */
+#define CBG_ERR_BAD_MATRIX (-7)   /* CSR row pointers not monotone or a column index out of range;
+                                     with the Jacobi preconditioner also a zero or missing
+                                     diagonal entry */
 #define CBG_ERR_STATE (-8)        /* stepwise call out of order (advance before start, ...) */
 
 /* ---- basis storage formats ------------------------------------------------------------------ */
