@@ -109,7 +109,8 @@ size_t cbg_basis_work_bytes(int64_t n, int32_t nvec);
  * block-fixed-point copy of w and accumulated in FP64 across blocks; cast formats accumulate in
  * FP64. Error bound: 2^-53 * sum_b max_{k in b}|w_k| * sum_{k in b}|vhat_k| plus FP64 summation
  * error over at most about 2^6 sequential terms. d_work: cbg_basis_work_bytes(n, nvec) bytes,
- * 256-byte aligned, no initial contents required, not used concurrently by another call. */
+ * 256-byte aligned, no initial contents required, not used concurrently by another call. Empty
+ * inputs: nvec = 0 writes nothing; n = 0 sets d_h[0..nvec) to 0 (the empty sums). */
 int cbg_basis_dot(const cbg_basis* basis, int32_t nvec, const double* d_w, double* d_h, void* d_work,
                   size_t work_bytes, void* stream);
 
@@ -130,7 +131,8 @@ int cbg_basis_dot_noalloc(const cbg_basis* basis, int32_t nvec, const double* d_
 /* d_w[k] -= sum_i vhat_i[k] * d_h[i] over i in [0, nvec): the update w := w - V_j h of Fig. 1
  * step 5 (highlighted). The sum over i is exact in integer arithmetic for FRSZ2 (h scaled per
  * block to a 54-bit fixed point), FP64 otherwise. If d_norm2 is not NULL it receives ||w||^2 after
- * the update (the norm of step 6). d_work as for cbg_basis_dot. */
+ * the update (the norm of step 6). d_work as for cbg_basis_dot. Empty inputs: with nvec = 0, w
+ * is left unchanged and *d_norm2 still receives ||w||^2; with n = 0, *d_norm2 receives 0. */
 int cbg_basis_update(const cbg_basis* basis, int32_t nvec, const double* d_h, double* d_w, double* d_norm2,
                      void* d_work, size_t work_bytes, void* stream);
 
@@ -173,10 +175,16 @@ typedef struct cbg_opts {
   int32_t precond;    /* the M of Fig. 1 steps 3 and 17, applied on the right: CBG_PRECOND_NONE
                          (M = I, the paper's setting, default) or CBG_PRECOND_JACOBI (M = diag(A);
                          a zero or missing diagonal entry ends the solve with CBG_ERR_BAD_MATRIX) */
-  int32_t reserved_;  /* must be 0 */
+  int32_t cycle;      /* how a restart cycle runs: CBG_CYCLE_AUTO (default) runs it as one
+                         thread-block cluster launch with the compressed basis in shared memory
+                         when the system is small enough (see cbgmres_cycle_cluster), else as
+                         the streamed kernels over the basis in device memory;
+                         CBG_CYCLE_STREAMED always streams. Both compute Fig. 1 with the same
+                         per-element arithmetic; only the order of FP64 sums differs. */
 } cbg_opts;
 
 enum { CBG_PRECOND_NONE = 0, CBG_PRECOND_JACOBI = 1 };
+enum { CBG_CYCLE_AUTO = 0, CBG_CYCLE_STREAMED = 1 };
 
 typedef struct cbg_result {
   int64_t iters;       /* Arnoldi steps (new basis vectors) */
@@ -306,6 +314,16 @@ int cbgmres_history(cbg_ctx* ctx, double* h_out, int64_t cap, int64_t* count);
  * because the restart never reads it, and later slots are unspecified. For inspection (value and
  * exponent distributions of the basis), not part of the solve. */
 int cbgmres_basis_vector(cbg_ctx* ctx, int32_t slot, double* d_out);
+
+/* How the context runs a restart cycle, decided at cbgmres_create from n, nnz and the options:
+ * 0 for the streamed kernels (one kernel per operation, the basis in device memory), or the number
+ * of CTAs (16 or 8) of the thread-block cluster that runs each whole cycle in one launch with its
+ * slice of the compressed basis in each CTA's shared memory. The cluster is chosen when
+ * opts.cycle is CBG_CYCLE_AUTO, the mean row length is below 12 (thread-per-row SpMV), restart +
+ * 1 <= 128 and one CTA's share of the basis fits in its shared memory (with restart 50: up to
+ * about 13 000 rows for FRSZ2-32, 7 000 for fp64). Returns -1 for a null context. In the
+ * stepwise API, cbgmres_advance then runs whole cycles, whatever max_steps asks. */
+int32_t cbgmres_cycle_cluster(const cbg_ctx* ctx);
 
 /* Frees the context's device memory. Accepts NULL. */
 int cbgmres_destroy(cbg_ctx* ctx);

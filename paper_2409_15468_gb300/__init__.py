@@ -18,6 +18,7 @@ from . import build as _build
 FP64, FP32, FP16, BF16, FRSZ2 = 0, 1, 2, 3, 4
 FORMATS = {"fp64": FP64, "fp32": FP32, "fp16": FP16, "bf16": BF16, "frsz2": FRSZ2}
 PRECOND = {"none": 0, "jacobi": 1}
+CYCLE = {"auto": 0, "streamed": 1}
 STATUS = {0: "CBG_OK", -1: "CBG_ERR_INVALID_ARG", -2: "CBG_ERR_CUDA", -3: "CBG_ERR_OOM", -4: "CBG_ERR_NONFINITE",
           -5: "CBG_ERR_NOT_CONVERGED", -6: "CBG_ERR_TIMEOUT", -7: "CBG_ERR_BAD_MATRIX", -8: "CBG_ERR_STATE"}
 ERR_NOT_CONVERGED = -5
@@ -28,7 +29,7 @@ EXPORTS = ["cbg_frsz2_bytes", "cbg_frsz2_compress", "cbg_frsz2_decompress", "cbg
            "cbg_csr_validate",
            "cbg_spmv_work_bytes", "cbg_spmv", "cbg_opts_default", "cbgmres_workspace_bytes", "cbgmres_create",
            "cbgmres_solve", "cbgmres_start", "cbgmres_advance", "cbgmres_finish", "cbgmres_history",
-           "cbgmres_destroy", "cbgmres_basis_vector", "cbg_server_create", "cbg_server_submit", "cbg_server_poll", "cbg_server_stats",
+           "cbgmres_destroy", "cbgmres_basis_vector", "cbgmres_cycle_cluster", "cbg_server_create", "cbg_server_submit", "cbg_server_poll", "cbg_server_stats",
            "cbg_server_clock", "cbg_server_destroy", "cbg_last_error", "cbg_version"]
 
 
@@ -41,7 +42,7 @@ class CbgError(RuntimeError):
 class Opts(ctypes.Structure):
     _fields_ = [("restart", ctypes.c_int32), ("fmt", ctypes.c_int32), ("frsz2_bits", ctypes.c_int32),
                 ("history", ctypes.c_int32), ("tol", ctypes.c_double), ("max_iters", ctypes.c_int64),
-                ("eta", ctypes.c_double), ("precond", ctypes.c_int32), ("reserved_", ctypes.c_int32)]
+                ("eta", ctypes.c_double), ("precond", ctypes.c_int32), ("cycle", ctypes.c_int32)]
 
 
 class Result(ctypes.Structure):
@@ -114,6 +115,7 @@ def load(path: str | None = None):
         "cbgmres_history": (c_int, [P, P, i64, ctypes.POINTER(i64)]),
         "cbgmres_destroy": (c_int, [P]),
         "cbgmres_basis_vector": (c_int, [P, i32, P]),
+        "cbgmres_cycle_cluster": (i32, [P]),
         "cbg_server_create": (c_int, [ctypes.POINTER(P), sz, i32, i32, i32]),
         "cbg_server_submit": (c_int, [P, ctypes.POINTER(Request)]),
         "cbg_server_poll": (c_int, [P, ctypes.POINTER(Completion), i32, ctypes.POINTER(i32)]),
@@ -296,6 +298,8 @@ def default_opts(**kw) -> Opts:
             v = FORMATS[v]
         if k == "precond" and isinstance(v, str):
             v = PRECOND[v]
+        if k == "cycle" and isinstance(v, str):
+            v = CYCLE[v]
         setattr(o, k, v)
     return o
 
@@ -362,6 +366,11 @@ class Solver:
         cnt = ctypes.c_int64(0)
         check(lib().cbgmres_history(self.handle, ctypes.c_void_p(buf.ctypes.data), cap, ctypes.byref(cnt)))
         return buf[: cnt.value]
+
+    @property
+    def cycle_cluster(self) -> int:
+        """CTAs of the cluster that runs each restart cycle on chip, or 0 (streamed cycles)."""
+        return int(lib().cbgmres_cycle_cluster(self.handle))
 
     def basis_vector(self, slot: int, out: torch.Tensor | None = None) -> torch.Tensor:
         """Basis vector `slot` of the context's current Krylov basis, decoded (ordered on the

@@ -17,7 +17,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libcbgmres.so")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
-SOURCES = ["capi.cu", "codec.cu", "basis.cu", "basis_frsz2.cu", "spmv.cu", "solver.cu", "noalloc.cu",
+SOURCES = ["capi.cu", "codec.cu", "basis.cu", "basis_frsz2.cu", "spmv.cu", "solver.cu", "onchip.cu", "noalloc.cu",
            "server.cu", "intensity.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-O2", "--expt-relaxed-constexpr",

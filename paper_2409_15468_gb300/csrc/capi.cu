@@ -278,7 +278,14 @@ int cbg_basis_update(const cbg_basis* basis, int32_t nvec, const double* d_h, do
                      void* d_work, size_t work_bytes, void* stream) {
   int st = check_basis(basis, nvec);
   if (st) return st;
-  if (basis->n == 0) return CBG_OK;
+  if (basis->n == 0) {  // an empty w: nothing to update, ||w||^2 = 0
+    if (d_norm2) {
+      if (!aligned(d_norm2, 8)) return bad("cbg_basis_update: misaligned norm pointer");
+      cudaError_t e = cudaMemsetAsync(d_norm2, 0, sizeof(double), static_cast<cudaStream_t>(stream));
+      if (e != cudaSuccess) return cuda_fail(e, "cbg_basis_update: zero fill");
+    }
+    return CBG_OK;
+  }
   if (!d_w || !aligned(d_w, 16) || (nvec > 0 && (!d_h || !aligned(d_h, 8))))
     return bad("cbg_basis_update: bad w or h pointer");
   DeviceInfo di;

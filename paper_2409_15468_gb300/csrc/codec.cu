@@ -15,6 +15,7 @@
 
 #include "common.cuh"
 #include "decode.cuh"
+#include "frsz2_block.cuh"
 #include "kernels.cuh"
 
 namespace cbg {
@@ -25,18 +26,6 @@ __device__ __forceinline__ bool gate_skip_c(const Gate& g) {
   if (g.stop && *(volatile const int*)g.stop) return true;
   if (g.need && !*(volatile const int*)g.need) return true;
   return false;
-}
-
-// Code of one value (Compression steps 2-5) given the block's effective maximum exponent.
-template <int L>
-__device__ __forceinline__ uint32_t make_code(uint64_t u, int ebar) {
-  const int e = static_cast<int>((u >> 52) & 0x7FF);
-  uint64_t m = u & ((1ull << 52) - 1);
-  if (e) m |= 1ull << 52;                     // step 2: explicit leading 1 (none for subnormals)
-  const int k = ebar - (e > 1 ? e : 1);       // step 3: number of prefixed zeros
-  const int sh = k + 54 - L;                  // steps 3-5: keep the first l-1 significand bits
-  const uint32_t S = sh < 64 ? static_cast<uint32_t>(m >> sh) : 0u;
-  return (static_cast<uint32_t>(u >> 63) << (L - 1)) | S;  // step 4: sign on the left
 }
 
 }  // namespace

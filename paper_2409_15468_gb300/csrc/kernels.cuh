@@ -131,6 +131,46 @@ int launch_cycle_init(SolverCtl* ctl, double* g, int m, int steps_allowed, cudaS
 int launch_intensity(const BasisView& B, int slot, int r, bool fp32_compute, double* partials, unsigned int* counter,
                      double* out, cudaStream_t stream);
 
+// ---- onchip.cu: a whole restart cycle in one thread-block cluster ------------------------------
+// Shared-memory layout of one CTA of the on-chip cycle (byte offsets; rows per CTA a multiple of 32).
+struct OcLayout {
+  int rows;
+  int slot_bytes;  // stride between basis slots
+  int exp_words;   // stride between slots' exponent words (FRSZ2)
+  int off_codes, off_exps, off_z, off_vec, off_state;
+  int off_csr;     // the CTA's CSR rows (values, columns, row offsets) when they fit in csr_bytes
+  int csr_bytes;
+  int bytes;       // dynamic shared memory per CTA
+};
+struct OnchipPlan {
+  int cluster;  // CTAs per cluster (16 or 8); 0: the system takes the streamed cycle
+  OcLayout lay;
+};
+struct OnchipArgs {
+  int n;
+  const int32_t* row_ptr;
+  const int32_t* col;
+  const double* vals;
+  const double* b;
+  double* x;           // x0 in, x_m out
+  const double* dinv;  // Jacobi M^{-1} = 1 / diag(A), or null
+  double* r;           // r0 = b - A x0 in (its norm and reciprocal in ctl), the next r out
+  BasisMut basis;      // receives the cycle's basis vectors (streamed layout)
+  SolverCtl* ctl;
+  double* hist;
+  int64_t hist_off;
+  int64_t hist_cap;
+  int m;
+  int steps_allowed;
+};
+// Decides whether the system (n rows, nnz nonzeros, options o) runs its cycles on chip: short
+// rows, restart + 1 <= 128, one CTA's slice of the basis within the opt-in shared memory and a
+// cluster of that size schedulable on the device. plan->cluster = 0 otherwise.
+int onchip_plan(int32_t n, int64_t nnz, const cbg_opts* o, OnchipPlan* plan);
+// One restart cycle (Fig. 1 steps 1-17) and the next residual: r and x updated, ctl's beta, rcp,
+// m_eff, reorth_count, m_ls, breakdown, implicit and err set, the basis written back.
+int launch_onchip_cycle(const OnchipPlan& plan, const OnchipArgs& a, int fmt, int l, cudaStream_t stream);
+
 // ---- solver contexts over caller-provided memory (solver.cu), used by the serving runtime ----
 size_t ctx_pinned_bytes();
 size_t ctx_device_bytes(int32_t n, const cbg_opts* opts);

@@ -84,9 +84,9 @@ __global__ void __launch_bounds__(32) k_givens(GivensArgs a, int j) {
     hcol[j + 1] = hn;
     col[j + 1] = hn;
     const bool breakdown = (hn == 0.0) || (reorth && hn < c->eta * sqrt(c->hn2_first));
-    for (int i = 0; i < j; ++i) {
-      const double t = scs[i] * col[i] + ssn[i] * col[i + 1];
-      col[i + 1] = -ssn[i] * col[i] + scs[i] * col[i + 1];
+    for (int i = 0; i < j; ++i) {  // written as explicit FMAs: the on-chip cycle rotates identically
+      const double t = fma(scs[i], col[i], ssn[i] * col[i + 1]);
+      col[i + 1] = fma(-ssn[i], col[i], scs[i] * col[i + 1]);
       col[i] = t;
     }
     const double x = col[j], y = col[j + 1];
@@ -228,6 +228,7 @@ struct cbg_ctx {
   double *dinv, *z;  // Jacobi preconditioner: 1 / diag(A) and the restart's V y (null without)
   int32_t *perm, *perm_scratch;  // SpMV row order by length (null when rows are short)
   bool perm_ready;
+  OnchipPlan oc;  // oc.cluster > 0: every cycle is one cluster launch (onchip.cu)
   SolverCtl* ctl;
   SolverCtl* ctl_host;  // pinned mirror
   double* bnorm2_host;  // pinned
@@ -263,7 +264,7 @@ bool opts_valid(int32_t n, const cbg_opts* o) {
   if (o->fmt < CBG_FP64 || o->fmt > CBG_FRSZ2) return false;
   if (o->fmt == CBG_FRSZ2 && o->frsz2_bits != 16 && o->frsz2_bits != 21 && o->frsz2_bits != 32) return false;
   if (o->precond != CBG_PRECOND_NONE && o->precond != CBG_PRECOND_JACOBI) return false;
-  if (o->reserved_ != 0) return false;
+  if (o->cycle != CBG_CYCLE_AUTO && o->cycle != CBG_CYCLE_STREAMED) return false;
   return true;
 }
 
@@ -337,18 +338,45 @@ GivensArgs givens_args(cbg_ctx* c) {
   return a;
 }
 
-// Residual r := b - A x into w with beta = ||r|| (step 1), then a pinned copy of the control block
-// and an event the host polls.
-int enqueue_residual(cbg_ctx* c) {
-  NormEpilogue epi{nullptr, c->ctl, kEpiResidual};
-  int st = launch_spmv(c->n, c->nnz, c->row_ptr, c->col, c->vals, c->x, c->w, c->b, c->perm, c->partials,
-                       &c->ctl->counters[kCtrSpmv], &c->ctl->err, epi, Gate{nullptr, nullptr}, c->stream);
-  if (st) return st;
+// A pinned copy of the control block and an event the host polls.
+int enqueue_readback(cbg_ctx* c) {
   cudaError_t e = cudaMemcpyAsync(c->ctl_host, c->ctl, sizeof(SolverCtl), cudaMemcpyDeviceToHost, c->stream);
   if (e != cudaSuccess) return cuda_fail(e, "control block copy");
   e = cudaEventRecord(c->ev, c->stream);
   if (e != cudaSuccess) return cuda_fail(e, "event record");
   return CBG_OK;
+}
+
+// Residual r := b - A x into w with beta = ||r|| (step 1), then the control-block readback.
+int enqueue_residual(cbg_ctx* c) {
+  NormEpilogue epi{nullptr, c->ctl, kEpiResidual};
+  int st = launch_spmv(c->n, c->nnz, c->row_ptr, c->col, c->vals, c->x, c->w, c->b, c->perm, c->partials,
+                       &c->ctl->counters[kCtrSpmv], &c->ctl->err, epi, Gate{nullptr, nullptr}, c->stream);
+  if (st) return st;
+  return enqueue_readback(c);
+}
+
+// A whole cycle as one cluster launch, ending with the next residual, then the readback.
+int enqueue_onchip_cycle(cbg_ctx* c) {
+  OnchipArgs a;
+  a.n = c->n;
+  a.row_ptr = c->row_ptr;
+  a.col = c->col;
+  a.vals = c->vals;
+  a.b = c->b;
+  a.x = c->x;
+  a.dinv = c->dinv;
+  a.r = c->w;
+  a.basis = c->basis;
+  a.ctl = c->ctl;
+  a.hist = c->hist;
+  a.hist_off = c->iters;
+  a.hist_cap = c->opts.history ? c->opts.max_iters : 0;
+  a.m = c->opts.restart;
+  a.steps_allowed = c->steps_allowed;
+  int st = launch_onchip_cycle(c->oc, a, c->opts.fmt, c->opts.frsz2_bits, c->stream);
+  if (st) return st;
+  return enqueue_readback(c);
 }
 
 // One Arnoldi step j (see the file comment).
@@ -462,6 +490,12 @@ int after_residual(cbg_ctx* c) {
   }
   const int64_t left = c->opts.max_iters - c->iters;
   c->steps_allowed = static_cast<int>(left < c->opts.restart ? left : c->opts.restart);
+  if (c->oc.cluster > 0) {
+    st = enqueue_onchip_cycle(c);
+    if (st) return ctx_fail(c, st);
+    c->phase = kWaitResidual;
+    return CBG_OK;
+  }
   st = launch_cycle_init(c->ctl, c->g, c->opts.restart, c->steps_allowed, c->stream);
   if (st) return ctx_fail(c, st);
   // v_1 := r0 / beta, stored as basis vector 0 (step 1)
@@ -549,6 +583,11 @@ int ctx_create_in(cbg_ctx** out, int32_t n, int64_t nnz, const int32_t* d_row_pt
   c->perm = long_rows ? reinterpret_cast<int32_t*>(base + L.off_perm) : nullptr;
   c->perm_scratch = long_rows ? reinterpret_cast<int32_t*>(base + L.off_perm_scratch) : nullptr;
   c->perm_ready = false;
+  st = onchip_plan(n, nnz, &c->opts, &c->oc);
+  if (st) {
+    delete c;
+    return st;
+  }
   c->ctl_host = static_cast<SolverCtl*>(pinned);
   c->bnorm2_host = reinterpret_cast<double*>(static_cast<uint8_t*>(pinned) + sizeof(SolverCtl) + 16);
   cudaError_t e = cudaEventCreateWithFlags(&c->ev, cudaEventDisableTiming);
@@ -621,7 +660,7 @@ int cbg_opts_default(cbg_opts* o) {
   o->max_iters = 20000;
   o->eta = 0.70710678118654752440;
   o->precond = CBG_PRECOND_NONE;
-  o->reserved_ = 0;
+  o->cycle = CBG_CYCLE_AUTO;
   return CBG_OK;
 }
 
@@ -859,6 +898,8 @@ int cbgmres_basis_vector(cbg_ctx* c, int32_t slot, double* d_out) {
   }
   return launch_load(view_of(c), slot, d_out, c->stream);
 }
+
+int32_t cbgmres_cycle_cluster(const cbg_ctx* c) { return c ? c->oc.cluster : -1; }
 
 int cbgmres_destroy(cbg_ctx* c) {
   ctx_release(c);

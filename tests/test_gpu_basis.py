@@ -152,3 +152,34 @@ def test_update_many_groups(cbg, orc, l, nvec):
     tol = 4 * (2.0 ** -50 * (np.abs(w) + terms.sum(axis=0)) + nvec * 2.0 ** -53 * tmax) + 1e-300
     err = np.abs(out - ref)
     assert np.all(err <= tol), (err / tol).max()
+
+
+@pytest.mark.parametrize("fmt,l", [(0, 32), (1, 32), (4, 21), (4, 32)])
+def test_empty_inputs(cbg, orc, fmt, l):
+    """The degenerate sizes of the Gram-Schmidt pass: no basis vectors (nvec = 0) and empty vectors
+    (n = 0). With nvec = 0 the dot writes nothing and the update leaves w as it is but still
+    reports ||w||^2; with n = 0 every sum is empty: h = 0 and ||w||^2 = 0."""
+    n = 4096 + 45
+    B = cbg.BasisStorage(n, 3, fmt, l)
+    w = torch.from_numpy(np.random.default_rng(5).standard_normal(n)).cuda()
+    w0 = w.clone()
+    h = torch.full((4,), 7.0, dtype=torch.float64, device="cuda")
+    nrm = torch.full((1,), -1.0, dtype=torch.float64, device="cuda")
+    B.dot(0, w, out=h)
+    B.update(0, h, w, norm2=nrm)
+    torch.cuda.synchronize()
+    assert torch.equal(h, torch.full_like(h, 7.0))
+    assert torch.equal(w, w0)
+    wh = w0.cpu().numpy()
+    ref = orc.dot2(wh, wh)
+    assert abs(nrm.item() - ref) <= 1e-14 * ref
+
+    B0 = cbg.BasisStorage(0, 3, fmt, l)
+    e = torch.empty(8, dtype=torch.float64, device="cuda")[:0]
+    B0.store(0, e)
+    B0.dot(3, e, out=h)
+    nrm.fill_(-1.0)
+    B0.update(3, h, e, norm2=nrm)
+    torch.cuda.synchronize()
+    assert h[:3].tolist() == [0.0, 0.0, 0.0] and h[3].item() == 7.0
+    assert nrm.item() == 0.0
