@@ -126,6 +126,57 @@ struct GivensArgs {
 int launch_givens(const GivensArgs& a, int j, cudaStream_t stream);
 int launch_cycle_init(SolverCtl* ctl, double* g, int m, int steps_allowed, cudaStream_t stream);
 
+// Applies the rotations 0..j-1 of the least-squares update (Fig. 1 step 17) to col[0..j], called
+// by all 32 lanes of one warp: col[i] := c_i x_i + s_i y_i and x_{i+1} := -s_i x_i + c_i y_i, with
+// x_0 = col[0] and y_i the entry col[i+1] before the rotations, each as one FMA on a product that
+// does not depend on x. Returns x_j (col[j] holds it too). GB300's FP64 pipe spends ~64 cycles on
+// every warp instruction however few lanes are active, so the products (p, q: j doubles of
+// scratch each) and the outputs take one instruction per 32 rotations across the lanes, and only
+// the carried FMA runs on one lane, its loads issued eight rotations ahead.
+__device__ __forceinline__ double rotate_column_warp(double* col, const double* cs, const double* sn, double* p,
+                                                     double* q, int j, int lane) {
+  for (int i = lane; i < j; i += 32) {
+    const double y = col[i + 1];
+    p[i] = cs[i] * y;
+    q[i] = sn[i] * y;
+  }
+  __syncwarp();
+  if (lane == 0 && j > 0) {
+    constexpr int B = 8;
+    double x = col[0];
+    double sv[B], pv[B];
+#pragma unroll
+    for (int u = 0; u < B; ++u) {
+      const int i = u < j ? u : j - 1;
+      sv[u] = sn[i];
+      pv[u] = p[i];
+    }
+    for (int i0 = 0; i0 < j; i0 += B) {
+      double sv2[B], pv2[B];
+#pragma unroll
+      for (int u = 0; u < B; ++u) {
+        const int i = i0 + B + u < j ? i0 + B + u : j - 1;
+        sv2[u] = sn[i];
+        pv2[u] = p[i];
+      }
+#pragma unroll
+      for (int u = 0; u < B; ++u) {
+        if (i0 + u < j) {
+          col[i0 + u] = x;  // x_i, turned into the output below
+          x = fma(-sv[u], x, pv[u]);
+        }
+        sv[u] = sv2[u];
+        pv[u] = pv2[u];
+      }
+    }
+    col[j] = x;
+  }
+  __syncwarp();
+  for (int i = lane; i < j; i += 32) col[i] = fma(cs[i], col[i], q[i]);
+  __syncwarp();
+  return col[j];
+}
+
 // ---- intensity.cu -------------------------------------------------------------------------------
 // *out = sum_k f^r(x_k) over stored vector `slot` (see cbg_intensity). partials: kMaxGrid doubles.
 int launch_intensity(const BasisView& B, int slot, int r, bool fp32_compute, double* partials, unsigned int* counter,

@@ -96,7 +96,7 @@ __device__ __forceinline__ double cast_at(const uint8_t* slot, int i) {
 
 // Per-CTA scalars of the cycle (identical in every CTA).
 struct OcState {
-  double omega2, hn2, hn2_first, rcp, implicit, beta2;
+  double omega2, hn2, hn2_first, rcp, implicit, beta2, xc, hn, hn_first;
   int stop, reorth, m_eff, breakdown, reorth_count, stored, m_ls, bad;
 };
 
@@ -166,21 +166,32 @@ __global__ void __launch_bounds__(kOcThreads, 1) k_cycle_onchip(OnchipArgs a, Oc
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
     if (lane == 0) s.red[warp] = v;
     __syncthreads();
-    if (t == 0) s.hp[buf * (M1 + 1) + slot] = sum8(s.red, 1);
+    if (warp == 0) {  // the warp sums, as a three-level tree over lanes 0-7
+      double r = lane < kOcWarps ? s.red[lane] : 0.0;
+#pragma unroll
+      for (int o = 1; o < kOcWarps; o <<= 1) r += __shfl_xor_sync(0xffffffffu, r, o);
+      if (lane == 0) s.hp[buf * (M1 + 1) + slot] = r;
+    }
   };
   // out[i] = sum over the cluster's CTAs, in rank order, of their hp[buf][i], i < cnt.
   auto cluster_sum = [&](int cnt, double* out) {
     cluster_sync();
     const double* src = s.hp + buf * (M1 + 1);
-    for (int i = t; i < cnt; i += kOcThreads) {
-      double v[16];
+    // four lanes per value, each over four ranks, then two shuffle levels: a fixed pairwise tree
+    // over the 16 ranks (absent ranks add +0.0) in five FP64 instructions per warp
+    const int g = t & 3;
+    for (int i0 = 0; i0 < cnt; i0 += kOcThreads / 4) {
+      const int i = i0 + (t >> 2);
+      double v[4];
 #pragma unroll
-      for (uint32_t c = 0; c < 16; ++c) v[c] = c < nctas ? (c == rank ? src[i] : dsmem_ld(src + i, c)) : 0.0;
-#pragma unroll
-      for (int h = 8; h > 0; h >>= 1)  // a fixed pairwise tree over the ranks (absent ranks: +0.0)
-#pragma unroll
-        for (int c = 0; c < h; ++c) v[c] += v[c + h];
-      out[i] = v[0];
+      for (int k = 0; k < 4; ++k) {
+        const uint32_t c = static_cast<uint32_t>(4 * g + k);
+        v[k] = (i < cnt && c < nctas) ? (c == rank ? src[i] : dsmem_ld(src + i, c)) : 0.0;
+      }
+      double r = (v[0] + v[1]) + (v[2] + v[3]);
+      r += __shfl_xor_sync(0xffffffffu, r, 1);
+      r += __shfl_xor_sync(0xffffffffu, r, 2);
+      if (i < cnt && g == 0) out[i] = r;
     }
     buf ^= 1;
     __syncthreads();
@@ -510,22 +521,20 @@ __global__ void __launch_bounds__(kOcThreads, 1) k_cycle_onchip(OnchipArgs a, Oc
     // step 17, one column: h_{1:j+1} (+ u), h_{j+2,j+1} = ||w||, the previous rotations, a new one
     for (int i = t; i <= j; i += kOcThreads) s.col[i] = S.reorth ? s.h[i] + s.u[i] : s.h[i];
     __syncthreads();
+    // warp 0 applies the previous rotations while warp 1 takes the square roots: ||w|| and, for
+    // the breakdown test, ||w|| after the first pass
+    if (warp == 0) {
+      const double xr = rotate_column_warp(s.col, s.cs, s.sn, s.wpart, s.wpart + M1, j, lane);
+      if (lane == 0) S.xc = xr;
+    } else if (warp == 1 && lane < 2) {
+      const double q = sqrt(lane == 1 ? S.hn2_first : S.hn2);
+      if (lane == 1) S.hn_first = q;
+      else S.hn = q;
+    }
+    __syncthreads();
     if (warp == 0) {
       const bool reorth = S.reorth != 0;
-      // lanes 0 and 1: ||w|| and, for the breakdown test, ||w|| after the first pass
-      const double sq = sqrt(lane == 1 ? S.hn2_first : S.hn2);
-      const double hn = __shfl_sync(0xffffffffu, sq, 0), hn_first = __shfl_sync(0xffffffffu, sq, 1);
-      double xc = 0.0;
-      if (lane == 0) {  // the previous rotations; the chain through xc is one FMA per rotation
-        xc = s.col[0];
-#pragma unroll 4
-        for (int i = 0; i < j; ++i) {
-          const double yn = s.col[i + 1], ci = s.cs[i], si = s.sn[i];
-          s.col[i] = fma(ci, xc, si * yn);
-          xc = fma(-si, xc, ci * yn);
-        }
-      }
-      xc = __shfl_sync(0xffffffffu, xc, 0);
+      const double hn = S.hn, hn_first = S.hn_first, xc = S.xc;
       // the new rotation: lane 0 c = x / r, lane 1 s = h / r, lane 2 the next normalisation 1 / h
       const double r = hypot(xc, hn);
       const double num = lane == 0 ? xc : (lane == 1 ? hn : 1.0);

@@ -58,7 +58,7 @@ __global__ void k_set_bnorm(SolverCtl* ctl, const double* bnorm2, double tol, do
 constexpr int kMaxRestart = 1024;
 __global__ void __launch_bounds__(32) k_givens(GivensArgs a, int j) {
   __shared__ double col[kMaxRestart + 2];
-  __shared__ double scs[kMaxRestart], ssn[kMaxRestart];
+  __shared__ double scs[kMaxRestart], ssn[kMaxRestart], sp[kMaxRestart], sq[kMaxRestart];
   SolverCtl* c = a.ctl;
   if (*(volatile const int*)&c->stop) return;  // every lane reads it before lane 0 may write it
   const int lane = threadIdx.x;
@@ -78,28 +78,24 @@ __global__ void __launch_bounds__(32) k_givens(GivensArgs a, int j) {
     ssn[i] = a.sn[i];
   }
   __syncwarp();
+  // lanes 0 and 1: ||w|| and, for the breakdown test, ||w|| after the first pass (one instruction
+  // stream for both); then the previous rotations, across the warp
+  const double sqv = sqrt(lane == 1 ? c->hn2_first : c->hn2);
+  const double hn = __shfl_sync(0xffffffffu, sqv, 0), hn_first = __shfl_sync(0xffffffffu, sqv, 1);
+  const double x = rotate_column_warp(col, scs, ssn, sp, sq, j, lane), y = hn;
+  // the new rotation: lane 0 c = x / r, lane 1 s = y / r, lane 2 the next normalisation 1 / h
+  const double r = hypot(x, y);
+  const double num = lane == 0 ? x : (lane == 1 ? y : 1.0);
+  const double den = lane == 2 ? hn : r;
+  const double qv = (lane < 3 && den != 0.0) ? num / den : 0.0;
+  const double cs = y != 0.0 ? __shfl_sync(0xffffffffu, qv, 0) : 1.0;
+  const double sn = y != 0.0 ? __shfl_sync(0xffffffffu, qv, 1) : 0.0;
+  const double rcp = __shfl_sync(0xffffffffu, qv, 2);
   if (lane == 0) {
     if (reorth) c->reorth_count += 1;
-    const double hn = sqrt(c->hn2);
     hcol[j + 1] = hn;
-    col[j + 1] = hn;
-    const bool breakdown = (hn == 0.0) || (reorth && hn < c->eta * sqrt(c->hn2_first));
-    for (int i = 0; i < j; ++i) {  // written as explicit FMAs: the on-chip cycle rotates identically
-      const double t = fma(scs[i], col[i], ssn[i] * col[i + 1]);
-      col[i + 1] = fma(-ssn[i], col[i], scs[i] * col[i + 1]);
-      col[i] = t;
-    }
-    const double x = col[j], y = col[j + 1];
-    double cs, sn;
-    if (y == 0.0) {
-      cs = 1.0;
-      sn = 0.0;
-    } else {
-      const double r = hypot(x, y);
-      cs = x / r;
-      sn = y / r;
-      col[j] = r;
-    }
+    const bool breakdown = (hn == 0.0) || (reorth && hn < c->eta * hn_first);
+    col[j] = y != 0.0 ? r : x;
     col[j + 1] = 0.0;
     a.cs[j] = cs;
     a.sn[j] = sn;
@@ -115,7 +111,7 @@ __global__ void __launch_bounds__(32) k_givens(GivensArgs a, int j) {
       c->stop = 1;
     }
     if (breakdown || implicit <= c->tol || j + 1 >= c->steps_allowed) c->stop = 1;
-    c->rcp = hn > 0.0 ? 1.0 / hn : 0.0;
+    c->rcp = hn > 0.0 ? rcp : 0.0;
     c->reorth = 0;
   }
   __syncwarp();
