@@ -248,26 +248,33 @@ def time_e2e(pkg, torch, B, w, nvec, steps, warmup):
 
 def time_to_tol(pkg, torch, device, repeats=3):
     """Full CB-GMRES solves to a 1e-10 relative residual on the 64x64 convection-diffusion system
-    (restart 50), FRSZ2-32 vs fp64 basis, through cbgmres_solve with device-resident b and x."""
+    (restart 50), FRSZ2-32 vs fp64 basis, through cbgmres_solve with device-resident b and x. A
+    system this small runs each restart cycle as one thread-block cluster launch (the default,
+    cycle="auto"); the same solves with the streamed kernels (cycle="streamed") are timed beside
+    them. Per entry: median seconds of `repeats` solves after one warm-up, and us per Arnoldi step."""
     import workloads
 
     A = workloads.convdiff(64, 2, (1.0, 0.5), 10.0, device=device)
     xt = workloads.uniform_vector(A.n, 0, device=device)
     b = pkg.spmv(A.row_ptr, A.col, A.vals, xt).clone()
     out = {}
-    for fmt in ("fp64", "frsz2"):
-        S = pkg.Solver(A.row_ptr, A.col, A.vals, restart=50, tol=1e-10, fmt=fmt, frsz2_bits=32)
-        ts, r = [], None
-        for _ in range(repeats + 1):
-            x = torch.zeros(A.n, dtype=torch.float64, device=device)
-            torch.cuda.synchronize()
-            t0 = time.perf_counter()
-            r = S.solve(b, x)
-            ts.append(time.perf_counter() - t0)
-        S.close()
-        out[fmt] = {"seconds": float(np.median(ts[1:])), "iters": r.iters, "converged": r.converged,
-                    "true_rrn": r.true_rrn}
+    for cycle in ("auto", "streamed"):
+        for fmt in ("fp64", "frsz2"):
+            S = pkg.Solver(A.row_ptr, A.col, A.vals, restart=50, tol=1e-10, fmt=fmt, frsz2_bits=32, cycle=cycle)
+            ts, r = [], None
+            for _ in range(repeats + 1):
+                x = torch.zeros(A.n, dtype=torch.float64, device=device)
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                r = S.solve(b, x)
+                ts.append(time.perf_counter() - t0)
+            sec = float(np.median(ts[1:]))
+            key = fmt if cycle == "auto" else f"{fmt}_streamed"
+            out[key] = {"seconds": sec, "iters": r.iters, "converged": r.converged, "true_rrn": r.true_rrn,
+                        "us_per_step": sec / max(r.iters, 1) * 1e6, "cycle_cluster": S.cycle_cluster}
+            S.close()
     out["speedup_frsz2_vs_fp64"] = out["fp64"]["seconds"] / out["frsz2"]["seconds"]
+    out["speedup_onchip_vs_streamed_frsz2"] = out["frsz2_streamed"]["seconds"] / out["frsz2"]["seconds"]
     out["config"] = "2D 5-point convection-diffusion 64x64 (n=4096), wind (1,0.5)*10, b = A x_true, restart 50"
     return out
 
@@ -652,6 +659,8 @@ def main():
     ap.add_argument("--no-extras", action="store_true", help="skip the format sweep, e2e, solve and CPU legs")
     ap.add_argument("--serving-requests", type=int, default=100, help="requests of the serving leg (0 skips it)")
     ap.add_argument("--serving-nmax", type=float, default=1e6, help="largest request n of the serving leg")
+    ap.add_argument("--solve-c1", action="store_true", help="only the 64x64 solves to 1e-10 (on-chip and "
+                    "streamed cycles)")
     ap.add_argument("--solve-c3", default="", help="comma-separated basis formats (fp64, fp32, fp16, bf16, "
                     "frsz2_16, frsz2_21, frsz2_32): run only the full 256^3 solves to 1e-10 and print them")
     ap.add_argument("--solve-c4", default="", help="as --solve-c3, on the 4M-row power-law matrix")
@@ -728,8 +737,10 @@ def main():
             dist.barrier()
             dist.destroy_process_group()
         return
-    if args.solve_c3 or args.solve_c4:
+    if args.solve_c1 or args.solve_c3 or args.solve_c4:
         if rank == 0:
+            if args.solve_c1:
+                print(json.dumps({"solve_c1": time_to_tol(pkg, torch, device)}))
             if args.solve_c3:
                 print(json.dumps({"solve_c3": solve_c3(pkg, torch, device, args.solve_c3.split(","))}))
             if args.solve_c4:
