@@ -276,8 +276,9 @@ struct FUpd {
   static constexpr int kStages = S;
   static constexpr int kGroup = 32;
   // resident CTAs per SM the register allocation is capped for (measured per code width: l = 16
-  // is fastest with a few spills at 6, l = 21 with 4); the deep pipeline runs one CTA per SM
-  static constexpr int kMinBlocks = S == 12 ? 1 : (L == 32 ? 5 : (L == 21 ? 4 : 6));
+  // is fastest with a few spills at 6, l = 21 with 4; l = 32 runs 4 by shared memory and uses the
+  // registers for an early load of w); the deep pipeline runs one CTA per SM
+  static constexpr int kMinBlocks = S == 12 ? 1 : (L == 32 ? 4 : (L == 21 ? 4 : 6));
   static constexpr int kVecBytes = kBlocks * L * 4;
   static constexpr int kStageBytes = kVps * kVecBytes;
   // dynamic smem: stages | coefficient table [kGroup][kBlocks] (int2) | exponent words of one group
@@ -434,6 +435,18 @@ __global__ void __launch_bounds__(FUpd<L, SD>::kThreads, FUpd<L, SD>::kMinBlocks
     const int nbt = static_cast<int>(min((int64_t)NBT, b1 - tb0));
     const bool active = blk < nbt;
     const int64_t k0 = (tb0 + blk) * 32 + q * 8;  // first of this thread's 8 values
+    // l = 32: this thread's 8 values of w are loaded now and arrive while the tile streams (1% at
+    // l = 32; at l = 16 and 21 the registers are better spent on the pipeline)
+    double wpre[8];
+    if (L == 32 && active && k0 + 8 <= B.n) {
+      const double2* pw = reinterpret_cast<const double2*>(w + k0);
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        const double2 v = pw[i];
+        wpre[2 * i] = v.x;
+        wpre[2 * i + 1] = v.y;
+      }
+    }
     // sum over the groups so far, in units of 2^(rc - 2101 + gb)
     long long tacc[8];
 #pragma unroll
@@ -585,11 +598,16 @@ __global__ void __launch_bounds__(FUpd<L, SD>::kThreads, FUpd<L, SD>::kMinBlocks
       if (k0 + 8 <= B.n) {
         double2* p = reinterpret_cast<double2*>(w + k0);
         double cur[8];
+        if (L == 32) {
 #pragma unroll
-        for (int i = 0; i < 4; ++i) {
-          const double2 v = p[i];
-          cur[2 * i] = v.x;
-          cur[2 * i + 1] = v.y;
+          for (int i = 0; i < 8; ++i) cur[i] = wpre[i];
+        } else {
+#pragma unroll
+          for (int i = 0; i < 4; ++i) {
+            const double2 v = p[i];
+            cur[2 * i] = v.x;
+            cur[2 * i + 1] = v.y;
+          }
         }
 #pragma unroll
         for (int k = 0; k < 8; ++k) cur[k] = sub(cur[k], sw ? tv[k ^ 4] : tv[k]);
