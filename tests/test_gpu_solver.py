@@ -292,3 +292,24 @@ def test_onchip_cycle_plan(cbg):
     assert cbg.Solver(B.row_ptr, B.col, B.vals, restart=50, fmt="frsz2").cycle_cluster == 0
     P = workloads.powerlaw(3000, seed=2).to("cuda")  # long rows: the lanes-per-row SpMV
     assert cbg.Solver(P.row_ptr, P.col, P.vals, restart=50, fmt="frsz2").cycle_cluster == 0
+
+
+@pytest.mark.parametrize("fmt,l", [("frsz2", 21), ("frsz2", 32), ("fp32", 32)])
+def test_onchip_restart_100_parity(cbg, orc, fmt, l):
+    """Restart 100 on chip: four coefficient groups in the update, up to four vectors per lane in
+    the dot, and cluster reductions of more than 64 values (two passes). Against the oracle: the
+    tolerance is reached, the iteration counts agree within 2% and the solutions to 1e-8."""
+    A = workloads.convdiff(60, 2, (1.0, -0.7), 20.0)
+    rp, col, vals = A.numpy()
+    b = orc.spmv(rp, col, vals, workloads.uniform_vector(A.n, 7).numpy())
+    ref = orc.gmres(rp, col, vals, b, restart=100, tol=1e-10, fmt=orc.FORMAT_NAMES[fmt], l=l)
+    assert ref.converged
+    Ad = A.to("cuda")
+    S = cbg.Solver(Ad.row_ptr, Ad.col, Ad.vals, restart=100, tol=1e-10, fmt=fmt, frsz2_bits=l)
+    assert S.cycle_cluster in (8, 16)
+    x = torch.zeros(A.n, dtype=torch.float64, device="cuda")
+    r = S.solve(torch.from_numpy(b).cuda(), x)
+    S.close()
+    assert r.converged and r.true_rrn <= 1e-10
+    assert abs(r.iters - ref.iters) <= max(1, 0.02 * ref.iters), (r.iters, ref.iters)
+    assert np.linalg.norm(x.cpu().numpy() - ref.x) / np.linalg.norm(ref.x) <= 1e-8
