@@ -127,54 +127,54 @@ int launch_givens(const GivensArgs& a, int j, cudaStream_t stream);
 int launch_cycle_init(SolverCtl* ctl, double* g, int m, int steps_allowed, cudaStream_t stream);
 
 // Applies the rotations 0..j-1 of the least-squares update (Fig. 1 step 17) to col[0..j], called
-// by all 32 lanes of one warp: col[i] := c_i x_i + s_i y_i and x_{i+1} := -s_i x_i + c_i y_i, with
-// x_0 = col[0] and y_i the entry col[i+1] before the rotations, each as one FMA on a product that
-// does not depend on x. Returns x_j (col[j] holds it too). GB300's FP64 pipe spends ~64 cycles on
-// every warp instruction however few lanes are active, so the products (p, q: j doubles of
-// scratch each) and the outputs take one instruction per 32 rotations across the lanes, and only
-// the carried FMA runs on one lane, its loads issued eight rotations ahead.
+// by all 32 lanes of one warp: col[i] := c_i x_i + s_i y_i with x_0 = col[0],
+// x_{i+1} = -s_i x_i + c_i y_i and y_i the entry col[i+1] before the rotations. Returns x_j
+// (col[j] holds it too). p and q are j doubles of scratch each.
+//
+// GB300's FP64 pipe spends ~64 cycles on every warp instruction however few lanes are active, so
+// the carried recurrence, an affine map per rotation, runs as a warp scan rather than a chain of
+// j FMAs. Lane l composes the maps of its K = ceil(j/32) consecutive rotations, five shuffle
+// levels compose them across the lanes, and each lane replays its rotations from the composed
+// start value: about 4K + 11 FP64 instructions per warp instead of j + 3. Every output and every
+// x_{i+1} is still one FMA on the products c_i y_i and s_i y_i. Only the start of each lane's
+// chunk is rounded in a different order than in a sequential pass.
 __device__ __forceinline__ double rotate_column_warp(double* col, const double* cs, const double* sn, double* p,
                                                      double* q, int j, int lane) {
+  const double x0 = col[0];
+  if (j <= 0) return x0;
   for (int i = lane; i < j; i += 32) {
     const double y = col[i + 1];
     p[i] = cs[i] * y;
     q[i] = sn[i] * y;
   }
   __syncwarp();
-  if (lane == 0 && j > 0) {
-    constexpr int B = 8;
-    double x = col[0];
-    double sv[B], pv[B];
-#pragma unroll
-    for (int u = 0; u < B; ++u) {
-      const int i = u < j ? u : j - 1;
-      sv[u] = sn[i];
-      pv[u] = p[i];
-    }
-    for (int i0 = 0; i0 < j; i0 += B) {
-      double sv2[B], pv2[B];
-#pragma unroll
-      for (int u = 0; u < B; ++u) {
-        const int i = i0 + B + u < j ? i0 + B + u : j - 1;
-        sv2[u] = sn[i];
-        pv2[u] = p[i];
-      }
-#pragma unroll
-      for (int u = 0; u < B; ++u) {
-        if (i0 + u < j) {
-          col[i0 + u] = x;  // x_i, turned into the output below
-          x = fma(-sv[u], x, pv[u]);
-        }
-        sv[u] = sv2[u];
-        pv[u] = pv2[u];
-      }
-    }
-    col[j] = x;
+  const int K = (j + 31) >> 5;
+  const int i0 = lane * K, i1 = min(j, i0 + K);
+  double A = 1.0, B = 0.0;  // this lane's rotations as x -> A x + B
+  for (int i = i0; i < i1; ++i) {
+    const double a = -sn[i];
+    B = fma(a, B, p[i]);
+    A = a * A;
   }
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {  // inclusive scan: the maps of lanes <= l, earlier ones first
+    const double Ap = __shfl_up_sync(0xffffffffu, A, d), Bp = __shfl_up_sync(0xffffffffu, B, d);
+    if (lane >= d) {
+      B = fma(A, Bp, B);
+      A = A * Ap;
+    }
+  }
+  double Ae = __shfl_up_sync(0xffffffffu, A, 1), Be = __shfl_up_sync(0xffffffffu, B, 1);
+  double x = lane == 0 ? x0 : fma(Ae, x0, Be);  // x at the start of this lane's rotations
+  for (int i = i0; i < i1; ++i) {
+    col[i] = fma(cs[i], x, q[i]);
+    x = fma(-sn[i], x, p[i]);
+  }
+  const double xj = __shfl_sync(0xffffffffu, x, (j - 1) / K);
   __syncwarp();
-  for (int i = lane; i < j; i += 32) col[i] = fma(cs[i], col[i], q[i]);
+  if (lane == 0) col[j] = xj;
   __syncwarp();
-  return col[j];
+  return xj;
 }
 
 // ---- intensity.cu -------------------------------------------------------------------------------

@@ -532,10 +532,15 @@ __global__ void __launch_bounds__(kOcThreads, 1) k_cycle_onchip(OnchipArgs a, Oc
       else S.hn = q;
     }
     __syncthreads();
+    // Warp 0 forms the new rotation and 1 / h_{j+2,j+1}, publishes the latter (named barrier 1:
+    // warp 0 arrives, the other warps wait), then finishes the column and the stop test while the
+    // other warps already store v_{j+2} = w / h_{j+2,j+1} (steps 13-14) into slot j + 1. The store
+    // is made on every step: on the last one it fills a slot the cycle does not read (the
+    // write-back stops at S.stored).
     if (warp == 0) {
       const bool reorth = S.reorth != 0;
       const double hn = S.hn, hn_first = S.hn_first, xc = S.xc;
-      // the new rotation: lane 0 c = x / r, lane 1 s = h / r, lane 2 the next normalisation 1 / h
+      // lane 0 c = x / r, lane 1 s = h / r, lane 2 the next normalisation 1 / h
       const double r = hypot(xc, hn);
       const double num = lane == 0 ? xc : (lane == 1 ? hn : 1.0);
       const double den = lane == 2 ? hn : r;
@@ -544,8 +549,7 @@ __global__ void __launch_bounds__(kOcThreads, 1) k_cycle_onchip(OnchipArgs a, Oc
       const double sn = hn != 0.0 ? __shfl_sync(0xffffffffu, q, 1) : 0.0;
       const double rcp = __shfl_sync(0xffffffffu, q, 2);
       if (lane == 0) {
-        const bool breakdown = (hn == 0.0) || (reorth && hn < eta * hn_first);  // step 12
-        if (reorth) S.reorth_count += 1;
+        S.rcp = hn > 0.0 ? rcp : 0.0;
         s.col[j] = hn != 0.0 ? r : xc;
         s.col[j + 1] = 0.0;
         s.cs[j] = c;
@@ -553,6 +557,12 @@ __global__ void __launch_bounds__(kOcThreads, 1) k_cycle_onchip(OnchipArgs a, Oc
         const double gj = s.g[j];
         s.g[j + 1] = -sn * gj;
         s.g[j] = c * gj;
+      }
+      __syncwarp();
+      asm volatile("bar.arrive 1, %0;" ::"n"(kOcThreads) : "memory");
+      if (lane == 0) {
+        const bool breakdown = (hn == 0.0) || (reorth && hn < eta * hn_first);  // step 12
+        if (reorth) S.reorth_count += 1;
         const double implicit = fabs(s.g[j + 1]) / bnorm;
         S.implicit = implicit;
         if (rank == 0 && a.hist && a.hist_off + j < a.hist_cap) a.hist[a.hist_off + j] = implicit;
@@ -563,16 +573,14 @@ __global__ void __launch_bounds__(kOcThreads, 1) k_cycle_onchip(OnchipArgs a, Oc
           S.stop = 1;
         }
         if (breakdown || implicit <= tol || j + 1 >= a.steps_allowed) S.stop = 1;
-        S.rcp = hn > 0.0 ? rcp : 0.0;
+        if (!S.stop) S.stored = j + 1;
       }
+      for (int i = lane; i <= j + 1; i += 32) s.Rm[(size_t)j * M1 + i] = s.col[i];
+    } else {
+      asm volatile("bar.sync 1, %0;" ::"n"(kOcThreads) : "memory");
     }
-    __syncthreads();
-    for (int i = t; i <= j + 1; i += kOcThreads) s.Rm[(size_t)j * M1 + i] = s.col[i];
-    if (!S.stop) {  // steps 13-14: v_{j+2} = w / h_{j+2,j+1} into slot j + 1
-      store(j + 1, S.rcp);
-      if (t == 0) S.stored = j + 1;
-      cluster_sync();  // every CTA's z is complete
-    }
+    store(j + 1, S.rcp);
+    cluster_sync();  // every CTA's z is complete, and S.stop is set
   }
   __syncthreads();
 
