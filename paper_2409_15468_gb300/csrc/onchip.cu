@@ -51,8 +51,11 @@ __device__ __forceinline__ uint32_t cluster_ctas() {
 }
 
 // Every thread of every CTA of the cluster arrives; shared-memory writes before it are visible to
-// distributed shared-memory reads after it.
+// distributed shared-memory reads after it. The barrier instructions are .aligned: every lane of a
+// warp must execute them together, so the warp is first reconverged (callers reach it straight
+// from loops in which only some lanes iterate).
 __device__ __forceinline__ void cluster_sync() {
+  __syncwarp();
   asm volatile(
       "barrier.cluster.arrive.release.aligned;\n\t"
       "barrier.cluster.wait.acquire.aligned;" ::
@@ -577,6 +580,7 @@ __global__ void __launch_bounds__(kOcThreads, 1) k_cycle_onchip(OnchipArgs a, Oc
       }
       for (int i = lane; i <= j + 1; i += 32) s.Rm[(size_t)j * M1 + i] = s.col[i];
     } else {
+      __syncwarp();  // bar.sync is .aligned
       asm volatile("bar.sync 1, %0;" ::"n"(kOcThreads) : "memory");
     }
     store(j + 1, S.rcp);
