@@ -100,7 +100,7 @@ __device__ __forceinline__ double cast_at(const uint8_t* slot, int i) {
 // Per-CTA scalars of the cycle (identical in every CTA).
 struct OcState {
   double omega2, hn2, hn2_first, rcp, implicit, beta2, xc, hn, hn_first;
-  int stop, reorth, m_eff, breakdown, reorth_count, stored, m_ls, bad;
+  int stop, reorth, m_eff, breakdown, reorth_count, stored, m_ls;
 };
 
 struct OcSmem {

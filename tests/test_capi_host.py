@@ -71,6 +71,13 @@ def test_invalid_arguments_rejected(pkg):
     assert L.cbg_basis_dot(ctypes.byref(b), 1, None, None, None, 0, None) == -1  # stride too small
     assert L.cbgmres_advance(None, 1, None) == -1
     assert L.cbgmres_destroy(None) == 0
+    # the cycle option takes CBG_CYCLE_AUTO (0) or CBG_CYCLE_STREAMED (1) only
+    assert pkg.default_opts().cycle == 0
+    assert pkg.workspace_bytes(1000, pkg.default_opts(cycle="streamed")) > 0
+    assert pkg.workspace_bytes(1000, pkg.default_opts(cycle=2)) == 0
+    bad = pkg.default_opts(cycle=-1)
+    assert L.cbgmres_create(ctypes.byref(h), 100, 0, None, None, None, ctypes.byref(bad), None) == -1
+    assert L.cbgmres_cycle_cluster(None) == -1
 
 
 @pytest.mark.skipif(torch.cuda.is_available(), reason="checks the behaviour without a CUDA device")
