@@ -10,7 +10,8 @@
 //  * the SpMV input z_j = M^{-1} v_j (FP64), read by the other CTAs through distributed shared
 //    memory (ld.shared::cluster) for the columns they need;
 //  * reductions (||w||^2 and V^T w): every CTA writes its partials, one cluster barrier follows,
-//    and every CTA sums the partials of all CTAs in rank order, so every CTA holds the same bits.
+//    and every CTA sums the partials of all CTAs in the same fixed pairwise tree over the ranks,
+//    so every CTA holds the same bits.
 // Every CTA then runs the Givens recurrence (step 17's rotations) and the back-substitution itself
 // on identical inputs, so the decisions (second pass, breakdown, convergence, step cap) agree in
 // every CTA: the cluster's control flow is uniform and every cluster barrier is reached by all of
@@ -163,7 +164,8 @@ __global__ void __launch_bounds__(kOcThreads, 1) k_cycle_onchip(OnchipArgs a, Oc
   const double eta = ctl->eta, bnorm = ctl->bnorm, tol = ctl->tol;
   int buf = 0;
 
-  // Sum over the CTA's threads of v into hp[buf][slot] (thread 0 adds the warp sums in order).
+  // Sum over the CTA's threads of v into hp[buf][slot]: a shuffle tree per warp, then warp 0 adds
+  // the eight warp sums as a three-level tree.
   auto cta_sum = [&](double v, int slot) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -176,7 +178,8 @@ __global__ void __launch_bounds__(kOcThreads, 1) k_cycle_onchip(OnchipArgs a, Oc
       if (lane == 0) s.hp[buf * (M1 + 1) + slot] = r;
     }
   };
-  // out[i] = sum over the cluster's CTAs, in rank order, of their hp[buf][i], i < cnt.
+  // out[i] = sum over the cluster's CTAs of their hp[buf][i], i < cnt, read through distributed
+  // shared memory after the barrier.
   auto cluster_sum = [&](int cnt, double* out) {
     cluster_sync();
     const double* src = s.hp + buf * (M1 + 1);
