@@ -275,6 +275,23 @@ def time_to_tol(pkg, torch, device, repeats=3):
             S.close()
     out["speedup_frsz2_vs_fp64"] = out["fp64"]["seconds"] / out["frsz2"]["seconds"]
     out["speedup_onchip_vs_streamed_frsz2"] = out["frsz2_streamed"]["seconds"] / out["frsz2"]["seconds"]
+    # every storage format on chip (one warm-up, then the median of `repeats` solves)
+    fmts = {}
+    for name, fmt, bits in (("fp64", "fp64", 32), ("fp32", "fp32", 32), ("fp16", "fp16", 32), ("bf16", "bf16", 32),
+                            ("frsz2_16", "frsz2", 16), ("frsz2_21", "frsz2", 21), ("frsz2_32", "frsz2", 32)):
+        S = pkg.Solver(A.row_ptr, A.col, A.vals, restart=50, tol=1e-10, fmt=fmt, frsz2_bits=bits)
+        ts, r = [], None
+        for _ in range(repeats + 1):
+            x = torch.zeros(A.n, dtype=torch.float64, device=device)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            r = S.solve(b, x)
+            ts.append(time.perf_counter() - t0)
+        sec = float(np.median(ts[1:]))
+        fmts[name] = {"seconds": sec, "iters": r.iters, "converged": r.converged, "true_rrn": r.true_rrn,
+                      "us_per_step": sec / max(r.iters, 1) * 1e6, "cycle_cluster": S.cycle_cluster}
+        S.close()
+    out["formats_on_chip"] = fmts
     out["config"] = "2D 5-point convection-diffusion 64x64 (n=4096), wind (1,0.5)*10, b = A x_true, restart 50"
     return out
 
