@@ -313,3 +313,26 @@ def test_onchip_restart_100_parity(cbg, orc, fmt, l):
     assert r.converged and r.true_rrn <= 1e-10
     assert abs(r.iters - ref.iters) <= max(1, 0.02 * ref.iters), (r.iters, ref.iters)
     assert np.linalg.norm(x.cpu().numpy() - ref.x) / np.linalg.norm(ref.x) <= 1e-8
+
+
+@pytest.mark.parametrize("cycle", ["auto", "streamed"])
+@pytest.mark.parametrize("N,dim", [(1, 2), (3, 2), (2, 3)])
+def test_tiny_systems(cbg, orc, cycle, N, dim):
+    """Degenerate sizes: n = 1, 9 and 8 rows with restart = n. On chip, fifteen of the sixteen CTAs
+    own no rows and the one block is partial. Against the oracle with the same FRSZ2-32 basis:
+    tolerance 1e-12 reached, iteration counts within 2 (1, 12 and 10 for the oracle), solutions
+    within 1e-10."""
+    A = workloads.convdiff(N, dim, tuple([1.0] * dim), 5.0)
+    rp, col, vals = A.numpy()
+    b = orc.spmv(rp, col, vals, workloads.uniform_vector(A.n, 11).numpy())
+    ref = orc.gmres(rp, col, vals, b, restart=A.n, tol=1e-12, fmt=orc.FRSZ2, l=32)
+    assert ref.converged
+    Ad = A.to("cuda")
+    S = cbg.Solver(Ad.row_ptr, Ad.col, Ad.vals, restart=A.n, tol=1e-12, fmt="frsz2", frsz2_bits=32, cycle=cycle)
+    assert (S.cycle_cluster in (8, 16)) if cycle == "auto" else S.cycle_cluster == 0
+    x = torch.zeros(A.n, dtype=torch.float64, device="cuda")
+    r = S.solve(torch.from_numpy(b).cuda(), x)
+    S.close()
+    assert r.converged and r.true_rrn <= 1e-12
+    assert abs(r.iters - ref.iters) <= 2, (r.iters, ref.iters)
+    assert np.linalg.norm(x.cpu().numpy() - ref.x) / np.linalg.norm(ref.x) <= 1e-10
