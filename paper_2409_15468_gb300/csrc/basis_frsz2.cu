@@ -260,8 +260,9 @@ __global__ void __launch_bounds__(FDot<L>::kThreads) k_dot_frsz2(BasisView B, in
 }
 
 // ================================================================================================
-// update: 8 consecutive values per thread, 4 threads per block, 32 blocks per tile, four basis
-// vectors per pipeline stage, vectors in groups of at most 32 (the exact integer sums are per group)
+// update: 8 consecutive values per thread, 4 threads per block, 32 blocks per tile (64 at l = 16),
+// four basis vectors per pipeline stage, vectors in groups of at most 32 (the exact integer sums
+// are per group)
 // ================================================================================================
 
 // S pipeline stages of 4 vectors: 2 when the grid fills the GPU (occupancy matters); 12 when it
@@ -269,16 +270,19 @@ __global__ void __launch_bounds__(FDot<L>::kThreads) k_dot_frsz2(BasisView B, in
 // the latency).
 template <int L, int S = 2>
 struct FUpd {
-  static constexpr int kThreads = 128;
-  static constexpr int kWarps = 4;
-  static constexpr int kBlocks = 32;
+  // 128 threads and 32-block tiles (4 KB of l = 32 codes per vector and stage); at l = 16, 256
+  // threads and 64-block tiles, whose larger copies measured 2.7% faster there (and 2.3% slower at
+  // l = 32); the deep pipeline keeps 128
+  static constexpr int kThreads = (S != 12 && L == 16) ? 256 : 128;
+  static constexpr int kWarps = kThreads / 32;
+  static constexpr int kBlocks = kThreads / 4;
   static constexpr int kVps = 4;  // basis vectors per stage
   static constexpr int kStages = S;
   static constexpr int kGroup = 32;
-  // resident CTAs per SM the register allocation is capped for (measured per code width: l = 16
-  // is fastest with a few spills at 6, l = 21 with 4; l = 32 runs 4 by shared memory and uses the
-  // registers for an early load of w); the deep pipeline runs one CTA per SM
-  static constexpr int kMinBlocks = S == 12 ? 1 : (L == 32 ? 4 : (L == 21 ? 4 : 6));
+  // resident CTAs per SM the register allocation is capped for (measured per code width: l = 16,
+  // at 256 threads, with a few spills at 3; l = 21 with 4; l = 32 runs 4 by shared memory and uses
+  // the registers for an early load of w); the deep pipeline runs one CTA per SM
+  static constexpr int kMinBlocks = S == 12 ? 1 : (L == 32 ? 4 : (L == 21 ? 4 : 3));
   static constexpr int kVecBytes = kBlocks * L * 4;
   static constexpr int kStageBytes = kVps * kVecBytes;
   // dynamic smem: stages | coefficient table [kGroup][kBlocks] (int2) | exponent words of one group
@@ -701,10 +705,11 @@ int frsz2_update_launch_t(const BasisView& B, int nvec, const int* nvec_dev, con
   const void* fn = fnp(k_update_frsz2<L, S>);
   const size_t smem = FUpd<L, S>::smem_bytes(nvec);
   int g;
-  int st = basis_launch_config(fn, 128, smem, (B.n + 31) / 32, 8, kMaxGrid, &g, nullptr);
+  constexpr int T = FUpd<L, S>::kThreads;
+  int st = basis_launch_config(fn, T, smem, (B.n + 31) / 32, T / 16, kMaxGrid, &g, nullptr);
   if (st) return st;
   if (grid > 0 && grid < g) g = grid;
-  k_update_frsz2<L, S><<<g, 128, smem, stream>>>(B, nvec, nvec_dev, h, negate, w, partials, counter, err, epi, gate);
+  k_update_frsz2<L, S><<<g, T, smem, stream>>>(B, nvec, nvec_dev, h, negate, w, partials, counter, err, epi, gate);
   cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? CBG_OK : cuda_fail(e, "frsz2 update launch");
 }
