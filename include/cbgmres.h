@@ -224,6 +224,8 @@ int cbgmres_solve(cbg_ctx* ctx, const double* d_b, double* d_x, cbg_result* resu
  *   cbgmres_start    computes the initial residual and the first basis vector (Fig. 1 step 1);
  *   cbgmres_advance  runs up to max_steps further Arnoldi steps, restarts included, and reports
  *                    in *done whether the solve has finished (converged, failed or out of steps);
+ *                    a context whose cycles run on chip (cbgmres_cycle_cluster > 0) runs whole
+ *                    restart cycles, one per call, whatever max_steps;
  *   cbgmres_finish   fills the result and returns the solve's status.
  * b and x must stay valid from start to finish. advance never waits on the device: at the end of
  * each cycle it polls an event and returns CBG_OK with *done = 0 until the restart's residual
@@ -238,8 +240,9 @@ int cbgmres_finish(cbg_ctx* ctx, cbg_result* result);
  * pinned control blocks of its slots. Requests are queued by cbg_server_submit without GPU work.
  * Every cbg_server_poll is one scheduling turn:
  *   1. each admitted solve is advanced by up to steps_per_turn Arnoldi steps on its own stream
- *      (cbgmres_advance; at most one earlier turn's work may still be in flight per slot, so the
- *      host never runs far ahead of the device and never blocks on a full launch queue);
+ *      (cbgmres_advance; a solve whose cycles run on chip advances by one whole restart cycle;
+ *      at most one earlier turn's work may still be in flight per slot, so the host never runs
+ *      far ahead of the device and never blocks on a full launch queue);
  *   2. finished solves release their slot and their workspace, and are reported as completions;
  *   3. queued requests are admitted in arrival order while a slot is free and their workspace
  *      (cbgmres_workspace_bytes) fits in the free budget. A request that does not fit is
