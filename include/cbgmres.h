@@ -224,8 +224,9 @@ int cbgmres_solve(cbg_ctx* ctx, const double* d_b, double* d_x, cbg_result* resu
  *   cbgmres_start    computes the initial residual and the first basis vector (Fig. 1 step 1);
  *   cbgmres_advance  runs up to max_steps further Arnoldi steps, restarts included, and reports
  *                    in *done whether the solve has finished (converged, failed or out of steps);
- *                    a context whose cycles run on chip (cbgmres_cycle_cluster > 0) runs whole
- *                    restart cycles, one per call, whatever max_steps;
+ *                    a context whose cycles run on chip (cbgmres_cycle_cluster > 0) advances by
+ *                    whole restart cycles whatever max_steps: a call launches the next cycle
+ *                    once the previous one has finished;
  *   cbgmres_finish   fills the result and returns the solve's status.
  * b and x must stay valid from start to finish. advance never waits on the device: at the end of
  * each cycle it polls an event and returns CBG_OK with *done = 0 until the restart's residual
