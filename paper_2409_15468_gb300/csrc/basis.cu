@@ -124,8 +124,10 @@ __global__ void __launch_bounds__(CastCfg::kThreads) k_dot_cast(BasisView B, int
       }
       const int vi = vec - v_lo;
       red[((batch & 1) * R + (vi % R)) * T + t] = hp;
-      __syncthreads();
+      // one barrier per batch of R vectors: each vector has its own slot, and a buffer is written
+      // again two batches later, after every thread has passed the next batch's barrier
       if (vi % R == R - 1 || vec == v_hi - 1) {
+        __syncthreads();
         const int first = vec - (vi % R);
         for (int vv = first + warp; vv <= vec; vv += T / 32) {
           const double* r = red + ((batch & 1) * R + ((vv - v_lo) % R)) * T;
