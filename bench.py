@@ -15,8 +15,8 @@ oracle timed on host cores on a bounded sample (cpu_baseline), the same step thr
 buffers (e2e), the other storage formats, and the time to a 1e-10 relative residual of a full
 CB-GMRES solve with the FRSZ2 and the fp64 basis.
 
-`--impl reference` times the oracle (plain C, one host core) on a bounded sample of the same
-step. Under torchrun (N > 1) every rank runs its own replica of the workload (weak scaling, no
+`--impl reference` times the oracle (plain C, its rows split over the host's cores) on a bounded
+sample of the same step. Under torchrun (N > 1) every rank runs its own replica of the workload (weak scaling, no
 collective on the data path); rank 0 prints the line.
 """
 from __future__ import annotations
@@ -296,14 +296,25 @@ def time_to_tol(pkg, torch, device, repeats=3):
     return out
 
 
+def stored_oracle_solve(matrix: str, fmt: str):
+    """The oracle's own solve of the full-size system, as committed under tests/golden/ by
+    tests/golden/make_solve_references.py (the oracle takes hours at this size), or None."""
+    path = os.path.join(ROOT, "tests", "golden", f"solve_{matrix}_{fmt}.json")
+    if not os.path.exists(path):
+        return None
+    with open(path) as f:
+        return json.load(f)
+
+
 def solve_c3(pkg, torch, device, formats, N: int = 256, restart: int = 100, tol: float = 1e-10,
-             max_iters: int = 20000, verify: bool = True, matrix: str = "c3"):
+             max_iters: int = 20000, matrix: str = "c3"):
     """Full CB-GMRES(restart) solves to a relative residual of tol, one per basis format, through
     cbgmres_solve with device-resident b = A 1 and x0 = 0, on
       c3: the 3D 7-point convection-diffusion system on an N^3 grid (wind (1,1,1), Peclet 50);
       c4: the 4M-row power-law random matrix (row lengths Pareto, mean ~30, max 2000; seed 2).
-    Each final x is checked on the host with the oracle's SpMV and compensated dot:
-    ||b - A x|| / ||b|| recomputed independently of the GPU path."""
+    Each result is set against the oracle's solve of the same system stored in tests/golden/ when
+    there is one: the step-count difference, the second passes, and the relative difference of x
+    at the stored sample of indices."""
     import workloads
 
     if matrix == "c4":
@@ -314,14 +325,6 @@ def solve_c3(pkg, torch, device, formats, N: int = 256, restart: int = 100, tol:
         A = workloads.convdiff(N, 3, (1.0, 1.0, 1.0), 50.0, device=device)
         desc = f"3D 7-point convection-diffusion {N}^3 (n={A.n}, nnz={A.nnz}), wind (1,1,1)*50"
     b = pkg.spmv(A.row_ptr, A.col, A.vals, torch.ones(A.n, dtype=torch.float64, device=device)).clone()
-    host = None
-    if verify:
-        import oracle
-
-        oracle.build()
-        rp, col, vals = A.numpy()
-        bh = b.cpu().numpy()
-        host = (oracle, rp, col, vals, bh, oracle.nrm2(bh))
     out = {"config": f"{desc}, b = A*1, x0 = 0, restart {restart}, tol {tol}, max_iters {max_iters}"}
     # SpMV alone (algorithmic bytes: values and column indices, row pointers, x once, y)
     y = torch.empty_like(b)
@@ -347,11 +350,18 @@ def solve_c3(pkg, torch, device, formats, N: int = 256, restart: int = 100, tol:
         dt = time.perf_counter() - t
         S.close()
         res = {"seconds": dt, "iters": r.iters, "restarts": r.restarts, "reorths": r.reorths,
-               "converged": r.converged, "true_rrn": r.true_rrn, "ms_per_iter": 1e3 * dt / max(r.iters, 1)}
-        if host:
-            orc, rp, col, vals, bh, bn = host
-            xh = x.cpu().numpy()
-            res["oracle_checked_rrn"] = orc.nrm2(bh - orc.spmv(rp, col, vals, xh)) / bn
+               "breakdowns": r.breakdowns, "converged": r.converged, "true_rrn": r.true_rrn,
+               "ms_per_iter": 1e3 * dt / max(r.iters, 1)}
+        ref = stored_oracle_solve(matrix, f) if restart == 100 and tol == 1e-10 and (matrix == "c4" or N == 256) \
+            else None
+        if ref:
+            idx = torch.tensor(ref["sample_index"], dtype=torch.int64, device=device)
+            xo = torch.tensor([float.fromhex(v) for v in ref["sample_x"]], dtype=torch.float64, device=device)
+            res["vs_oracle"] = {"oracle_iters": ref["iters"], "oracle_reorths": ref["reorths"],
+                                "iters_diff_pct": 100.0 * (r.iters - ref["iters"]) / ref["iters"],
+                                "x_rel_diff_at_samples": float(torch.linalg.vector_norm(x[idx] - xo) /
+                                                               torch.linalg.vector_norm(xo)),
+                                "oracle_true_rrn": ref["true_rrn"], "oracle_seconds_one_core": ref["oracle_seconds"]}
         out[f] = res
         del x
         torch.cuda.empty_cache()
@@ -608,46 +618,92 @@ def oracle_step_setup(n: int, nvec: int):
     return oracle, V, w
 
 
-def oracle_step(oracle, V, w, n, nvec):
+def oracle_step(oracle, V, w, n, nvec, pool=None, chunks=1):
     """The benchmark step on the host with the oracle as it stands: compress w, decode every stored
-    vector and take the sequential dot, then decode again and subtract (sequential axpy)."""
-    oracle.encode(w, oracle.FRSZ2, 32)
-    h = np.empty(nvec)
-    for i, (vals, exps) in enumerate(V):
-        h[i] = oracle.dot(oracle.decode(vals, exps, n, oracle.FRSZ2, 32), w)
-    for i, (vals, exps) in enumerate(V):
-        oracle.axpy(-h[i], oracle.decode(vals, exps, n, oracle.FRSZ2, 32), w)
-    return h, oracle.dot(w, w)
+    vector and take the sequential dot, then decode again and subtract (sequential axpy). With a
+    thread pool the rows are split into `chunks` ranges of whole 32-value blocks, each thread runs
+    the same oracle calls on its range (ctypes releases the interpreter lock), and every h_i is the
+    sum of the ranges' partial dots in range order, so the result does not depend on scheduling."""
+    if pool is None or chunks <= 1:
+        oracle.encode(w, oracle.FRSZ2, 32)
+        h = np.empty(nvec)
+        for i, (vals, exps) in enumerate(V):
+            h[i] = oracle.dot(oracle.decode(vals, exps, n, oracle.FRSZ2, 32), w)
+        for i, (vals, exps) in enumerate(V):
+            oracle.axpy(-h[i], oracle.decode(vals, exps, n, oracle.FRSZ2, 32), w)
+        return h, oracle.dot(w, w)
+    nb = (n + 31) // 32
+    bounds = [(nb * c // chunks, nb * (c + 1) // chunks) for c in range(chunks)]
+
+    def rows(b0, b1):
+        return b0 * 32, min(n, b1 * 32)
+
+    def part_dots(rng):
+        b0, b1 = rng
+        k0, k1 = rows(b0, b1)
+        oracle.encode(w[k0:k1], oracle.FRSZ2, 32)
+        return [oracle.dot(oracle.decode(vals[b0 * 32:b1 * 32], exps[b0:b1], k1 - k0, oracle.FRSZ2, 32), w[k0:k1])
+                for vals, exps in V]
+
+    parts = list(pool.map(part_dots, bounds))
+    h = np.array([sum(p[i] for p in parts) for i in range(nvec)])
+
+    def part_update(rng):
+        b0, b1 = rng
+        k0, k1 = rows(b0, b1)
+        wc = w[k0:k1]
+        for i, (vals, exps) in enumerate(V):
+            oracle.axpy(-h[i], oracle.decode(vals[b0 * 32:b1 * 32], exps[b0:b1], k1 - k0, oracle.FRSZ2, 32), wc)
+        return oracle.dot(wc, wc)
+
+    norms = list(pool.map(part_update, bounds))
+    return h, sum(norms)
 
 
-def oracle_rate(n: int, nvec: int, steps: int, warmup: int):
+def oracle_rate(n: int, nvec: int, steps: int, warmup: int, threads: int = 1):
+    from concurrent.futures import ThreadPoolExecutor
+
     oracle, V, w = oracle_step_setup(n, nvec)
-    for _ in range(warmup):
-        oracle_step(oracle, V, w, n, nvec)
-    t0 = time.perf_counter()
-    for _ in range(steps):
-        oracle_step(oracle, V, w, n, nvec)
-    dt = time.perf_counter() - t0
+    pool = ThreadPoolExecutor(threads) if threads > 1 else None
+    try:
+        for _ in range(warmup):
+            oracle_step(oracle, V, w, n, nvec, pool, threads)
+        t0 = time.perf_counter()
+        for _ in range(steps):
+            oracle_step(oracle, V, w, n, nvec, pool, threads)
+        dt = time.perf_counter() - t0
+    finally:
+        if pool:
+            pool.shutdown()
     byt = sum(step_bytes("frsz2", 32, n, nvec).values()) * steps
     return byt / dt / 1e9, dt
 
 
-def choose_oracle_sample(nvec: int, steps_total: int, budget_s: float, n_full: int) -> int:
-    """Largest sample (a multiple of 128 values) whose steps_total steps fit in budget_s."""
-    n0 = 4096
-    _, dt = oracle_rate(n0, nvec, 1, 0)
+def choose_oracle_sample(nvec: int, steps_total: int, budget_s: float, n_full: int, threads: int = 1) -> int:
+    """Largest sample (a multiple of 32 * threads * 4 values) whose steps_total steps fit in budget_s."""
+    n0 = 4096 * max(1, threads)
+    _, dt = oracle_rate(n0, nvec, 1, 0, threads)
     per_value = dt / n0
+    q = 128 * max(1, threads)
     n = int(budget_s / max(steps_total, 1) / per_value)
-    n = max(128, min(n_full, n // 128 * 128))
+    n = max(q, min(n_full, n // q * q))
     return n
 
 
 def cpu_baseline(n_full: int, nvec: int):
-    n = choose_oracle_sample(nvec, 3, 15.0, n_full)
-    gbs, dt = oracle_rate(n, nvec, 3, 0)
-    return {"value": gbs, "unit": "GB/s", "cores": 1, "kind": "oracle",
+    """The oracle on the host cores: on all of them (row ranges in threads, deterministic
+    reduction), and on one core, each on a bounded sample of the workload's rows."""
+    cores = os.cpu_count() or 1
+    n = choose_oracle_sample(nvec, 3, 12.0, n_full, cores)
+    gbs, dt = oracle_rate(n, nvec, 3, 0, cores)
+    n1 = choose_oracle_sample(nvec, 3, 8.0, n_full)
+    gbs1, dt1 = oracle_rate(n1, nvec, 3, 0)
+    return {"value": gbs, "unit": "GB/s", "cores": cores, "kind": "oracle",
             "sample": f"3 steps over {nvec} x {n} values ({n / n_full:.5f} of the workload's n), plain C oracle, "
-                      f"{dt:.1f} s", "nproc": os.cpu_count()}
+                      f"rows split over {cores} threads, {dt:.1f} s",
+            "nproc": cores,
+            "single_core": {"value": gbs1, "unit": "GB/s", "cores": 1,
+                            "sample": f"3 steps over {nvec} x {n1} values, {dt1:.1f} s"}}
 
 
 # ------------------------------------------------------------------------------------------------
@@ -706,15 +762,17 @@ def main():
     if args.impl == "reference":
         if rank != 0:
             return
-        n = choose_oracle_sample(args.nvec, args.steps + args.warmup, args.ref_budget, args.n)
-        gbs, dt = oracle_rate(n, args.nvec, args.steps, args.warmup)
+        cores = os.cpu_count() or 1
+        n = choose_oracle_sample(args.nvec, args.steps + args.warmup, args.ref_budget, args.n, cores)
+        gbs, dt = oracle_rate(n, args.nvec, args.steps, args.warmup, cores)
         line = {"impl": "reference", "metric": METRIC, "value": gbs, "unit": "GB/s", "n_gpus": args.gpus,
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3 / args.steps,
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
                 "data": "synthetic",
                 "config": {"workload": workload, "n": args.n, "nvec": args.nvec, "oracle_sample_n": n},
-                "cpu_baseline": {"value": gbs, "unit": "GB/s", "cores": 1, "kind": "oracle",
-                                 "sample": f"each step over {args.nvec} x {n} values of the workload"},
+                "cpu_baseline": {"value": gbs, "unit": "GB/s", "cores": cores, "kind": "oracle",
+                                 "sample": f"each step over {args.nvec} x {n} values of the workload, rows split "
+                                           f"over {cores} threads"},
                 "e2e": {"value": gbs, "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
         print(json.dumps(line))
         return
@@ -838,6 +896,7 @@ def main():
         line["formats"] = fmts
         line["time_to_tol"] = time_to_tol(pkg, torch, device)
         line["time_to_tol_c3"] = solve_c3(pkg, torch, device, ["frsz2_32", "fp64"])
+        line["time_to_tol_c4"] = solve_c3(pkg, torch, device, ["frsz2_32", "fp32", "fp64"], matrix="c4")
         if args.serving_requests > 0:
             line["serving"] = serving(pkg, torch, device, args.serving_requests, 1e4, args.serving_nmax)
         line["cpu_baseline"] = cpu_baseline(args.n, args.nvec)

@@ -39,6 +39,13 @@ extern "C" {
                                      with the Jacobi preconditioner also a zero or missing
                                      diagonal entry */
 #define CBG_ERR_STATE (-8)        /* stepwise call out of order (advance before start, ...) */
+#define CBG_ERR_BREAKDOWN_NOT_CONVERGED (-9) /* a restart cycle ended on Fig. 1 step 12 (breakdown) and
+                                     the explicit residual at the next restart was no smaller than at
+                                     the start of that cycle: the Krylov space stopped growing without
+                                     reaching tol (e.g. an inconsistent singular system). x and the
+                                     result are still written. */
+#define CBG_ERR_UNIMPLEMENTED (-10) /* a well-formed request this library does not implement: an
+                                     FRSZ2 code width l in [2, 32] other than 16, 21 and 32 */
 
 /* ---- basis storage formats ------------------------------------------------------------------ */
 typedef enum cbg_format {
@@ -63,13 +70,23 @@ int64_t cbg_frsz2_bytes(int64_t n, int32_t l);
 /* Compresses d_src[0..n) into d_exps[ceil(n/32)] and d_codes[ceil(n/32)*l] (Compression,
  * steps 1-6: one warp per 32-value block, warp-wide maximum of the exponent fields).
  * Inputs must be finite (Krylov values lie in [-1, 1]); the output for NaN or Inf is unspecified.
- * d_src must be 8-byte aligned, d_exps and d_codes 4-byte aligned. */
+ * d_src must be 8-byte aligned, d_exps and d_codes 4-byte aligned. Errors: CBG_ERR_UNIMPLEMENTED
+ * for a code width in [2, 32] other than 16, 21 and 32 (the format admits them; this library
+ * implements those three), CBG_ERR_INVALID_ARG for any other l or a negative n. */
 int cbg_frsz2_compress(const double* d_src, int64_t n, int32_t l, uint32_t* d_exps, uint32_t* d_codes,
                        void* stream);
 
-/* Decompresses into d_dst[0..n) (Decompression, steps 1-4; random access by block). */
+/* Decompresses into d_dst[0..n) (Decompression, steps 1-4; random access by block). Errors as for
+ * cbg_frsz2_compress. */
 int cbg_frsz2_decompress(const uint32_t* d_exps, const uint32_t* d_codes, int64_t n, int32_t l, double* d_dst,
                          void* stream);
+
+/* The codec under the plain names of the problem statement: the same functions as cbg_frsz2_bytes
+ * (returned as size_t, 0 for a bad n or l), cbg_frsz2_compress and cbg_frsz2_decompress. */
+size_t frsz2_bytes(int64_t n, int32_t l);
+int frsz2_compress(const double* d_src, int64_t n, int32_t l, uint32_t* d_exp, uint32_t* d_codes, void* stream);
+int frsz2_decompress(const uint32_t* d_exp, const uint32_t* d_codes, int64_t n, int32_t l, double* d_dst,
+                     void* stream);
 
 /* ---- basis layout --------------------------------------------------------------------------- *
  * A basis is nvec vectors of n values stored in one format. Vector i keeps its values (cast bits
@@ -95,6 +112,14 @@ int cbg_basis_layout(int64_t n, int32_t fmt, int32_t l, int64_t* vals_stride, in
 /* Stores d_src[0..n) as vector `slot` of the basis: FRSZ2 compression or a round-to-nearest-even
  * cast from FP64 (Fig. 1 steps 1 and 14, highlighted: appending a vector to the compressed basis). */
 int cbg_basis_store(const cbg_basis* basis, int32_t slot, const double* d_src, void* stream);
+
+/* Normalises and appends (Fig. 1 steps 13-14, and step 1 with h = beta): v := d_w / *d_h, each
+ * element the correctly rounded IEEE quotient (as the oracle divides), stored as vector `slot`
+ * exactly as cbg_basis_store would store v. d_h points to one double on the device, positive and
+ * finite (a norm); for other values of h the elements are d_w * RN(1/h). If d_v is not NULL it
+ * receives the FP64 v (the input of the next SpMV, step 3). d_w and d_v may be the same vector. */
+int cbg_basis_append(const cbg_basis* basis, int32_t slot, const double* d_w, const double* d_h, double* d_v,
+                     void* stream);
 
 /* Decodes basis vector `slot` into d_dst[0..n) (a read through the accessor: Implementation and
  * synthetic performance subsection). */
@@ -125,6 +150,12 @@ int cbg_basis_dot(const cbg_basis* basis, int32_t nvec, const double* d_w, doubl
  *     that device current; make that first call before any stream capture on the device.
  *   - Every call on a device uses the same array. Calls whose kernels overlap on the GPU (for
  *     example on two streams at once) race and produce wrong results; order them on one stream.
+ *     Each call clears the array's completion counter before its kernel runs; the partial sums
+ *     need no clearing (every slot a call reads is written by that call first).
+ *   - Empty inputs as for cbg_basis_dot: nvec = 0 writes nothing, n = 0 sets d_h[0..nvec) to 0.
+ *   - The FRSZ2 kernel bounds every wait on its bulk copies; should one expire, d_h is left
+ *     incomplete and, as for cbg_basis_dot, the device-side error word is not reported (the
+ *     copies complete with any valid basis, so this only happens on a faulting device).
  * Other arguments, results and the error bound are those of cbg_basis_dot. */
 int cbg_basis_dot_noalloc(const cbg_basis* basis, int32_t nvec, const double* d_w, double* d_h, void* stream);
 
@@ -167,7 +198,7 @@ int cbg_spmv(int32_t n, int64_t nnz, const int32_t* d_row_ptr, const int32_t* d_
 typedef struct cbg_opts {
   int32_t restart;    /* m, the number of basis vectors before a restart (Methodology: m = 100) */
   int32_t fmt;        /* cbg_format of the Krylov basis */
-  int32_t frsz2_bits; /* l for CBG_FRSZ2: 16, 21 or 32 */
+  int32_t frsz2_bits; /* l for CBG_FRSZ2: 16, 21 or 32 (another l in [2, 32]: CBG_ERR_UNIMPLEMENTED) */
   int32_t history;    /* nonzero: record the implicit relative residual after every Arnoldi step */
   double tol;         /* target relative residual ||b - A x|| / ||b|| (Eq. 4) */
   int64_t max_iters;  /* cap on Arnoldi steps */
@@ -195,6 +226,7 @@ typedef struct cbg_result {
   double true_rrn;     /* last explicit ||b - A x|| / ||b|| (Eq. 4) */
   double implicit_rrn; /* last |g_{j+1}| / ||b|| of the Givens recurrence */
   double seconds;      /* wall time of the solve as seen by the host */
+  int64_t breakdowns;  /* restart cycles that ended on the breakdown test of Fig. 1 step 12 */
 } cbg_result;
 
 typedef struct cbg_ctx cbg_ctx;
@@ -216,8 +248,10 @@ int cbgmres_create(cbg_ctx** out, int32_t n, int64_t nnz, const int32_t* d_row_p
 
 /* Solves A x = b (Fig. 1: restarted GMRES with the basis stored in opts->fmt). d_x holds x0 on
  * entry (the paper starts from x0 = 0) and the approximation on exit. Synchronises the stream.
- * Returns CBG_OK when converged, CBG_ERR_NOT_CONVERGED when max_iters was reached (x and *result
- * still valid), or another CBG_ERR_*. *result may be NULL. */
+ * Returns CBG_OK when converged, CBG_ERR_NOT_CONVERGED when max_iters was reached,
+ * CBG_ERR_BREAKDOWN_NOT_CONVERGED when a cycle that ended on a breakdown (step 12) left the
+ * explicit residual no smaller than it was at that cycle's start (x and *result still valid in
+ * both cases), or another CBG_ERR_*. *result may be NULL. */
 int cbgmres_solve(cbg_ctx* ctx, const double* d_b, double* d_x, cbg_result* result);
 
 /* Stepwise form of cbgmres_solve for a serving loop that interleaves several solves:
@@ -332,8 +366,10 @@ int32_t cbgmres_cycle_cluster(const cbg_ctx* ctx);
 /* Frees the context's device memory. Accepts NULL. */
 int cbgmres_destroy(cbg_ctx* ctx);
 
-/* Message of the last failed call on this thread ("" if none). */
+/* Message of the last failed call on this thread ("" if none). cbgmres_last_error is the same
+ * function under the name of the problem statement. */
 const char* cbg_last_error(void);
+const char* cbgmres_last_error(void);
 
 /* Library version string. */
 const char* cbg_version(void);

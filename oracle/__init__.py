@@ -53,7 +53,7 @@ class _Opts(ctypes.Structure):
 class _Result(ctypes.Structure):
     _fields_ = [("iters", ctypes.c_int64), ("restarts", ctypes.c_int64), ("reorths", ctypes.c_int64),
                 ("converged", ctypes.c_int32), ("breakdowns", ctypes.c_int32), ("true_rrn", ctypes.c_double),
-                ("implicit_rrn", ctypes.c_double)]
+                ("implicit_rrn", ctypes.c_double), ("stagnated", ctypes.c_int32)]
 
 
 def lib():
@@ -263,6 +263,7 @@ class GmresResult:
     implicit_rrn: float
     hist_implicit: np.ndarray
     hist_true: np.ndarray
+    stagnated: bool
 
 
 PRECOND = {"none": 0, "jacobi": 1}
@@ -295,7 +296,8 @@ def gmres(row_ptr, col, vals, b, x0=None, *, restart=50, tol=1e-10, max_iters=20
         raise ValueError(f"oracle gmres failed with status {st}")
     return GmresResult(x=x, iters=r.iters, restarts=r.restarts, reorths=r.reorths, converged=bool(r.converged),
                        breakdowns=r.breakdowns, true_rrn=r.true_rrn, implicit_rrn=r.implicit_rrn,
-                       hist_implicit=hi[:r.iters].copy(), hist_true=ht[:r.restarts + 1].copy())
+                       hist_implicit=hi[:r.iters].copy(), hist_true=ht[:r.restarts + 1].copy(),
+                       stagnated=bool(r.stagnated))
 
 
 def arnoldi_cycle(row_ptr, col, vals, b, x0=None, *, restart=50, tol=1e-300, fmt=FP64, l=32, eta=DEFAULT_ETA):

@@ -29,10 +29,19 @@
  *   R11 The least-squares problem of step 17 is solved with Givens rotations; the inner loop
  *       also ends when the implicit residual |g_{j+1}| reaches tol*||b||; convergence is only
  *       declared on the explicit residual at the start of a cycle.
- *   R12 Givens rotation: r = hypot(a, b), c = a/r, s = b/r; c = 1, s = 0 when b = 0.
+ *   R12 Givens rotation: r = sqrt(a*a + b*b), c = a/r, s = b/r; c = 1, s = 0 when b = 0. The
+ *       length is evaluated as IEEE operations in that order (after an exact power-of-two
+ *       scaling when the larger exponent field is above 1523 or below 523, i.e. outside
+ *       [2^-500, 2^501)), not with a library hypot: hypot's rounding differs between C libraries,
+ *       which would make the oracle's results depend on the host it runs on.
  *   R13 b = 0 gives x = 0 with RRN 0.
  *   R14 A zero diagonal entry of the rotated Hessenberg matrix truncates the least-squares
  *       solve to the leading columns before it.
+ *   R18 Fig. 1 says nothing of what follows a breakdown beyond ending the Arnoldi loop: the
+ *       least-squares update and the restart run as usual, and when the explicit residual at the
+ *       next restart is no smaller than at the start of the cycle that broke down, the Krylov
+ *       space has stopped growing; the solve then stops (stagnated) instead of repeating that
+ *       cycle until max_iters.
  */
 #include "oracle.h"
 
@@ -366,6 +375,17 @@ static void store_basis(cycle_ws* ws, int slot, const double* v) {
   orc_decode(vals, ex, ws->n, ws->fmt, ws->l, ws->vhat + (size_t)slot * ws->n);
 }
 
+/* The length of (a, b) for the Givens rotation (R12). */
+static double givens_radius(double a, double b) {
+  int ea = (int)((d2u(a) >> 52) & 0x7FF), eb = (int)((d2u(b) >> 52) & 0x7FF);
+  int e = ea > eb ? ea : eb;
+  double scale = 1.0;
+  if (e > 1523) scale = 0x1p-600;
+  else if (e < 523) scale = 0x1p600;
+  double as = a * scale, bs = b * scale;
+  return sqrt(as * as + bs * bs) / scale;
+}
+
 /* One cycle from the residual r with norm beta (Fig. 1 steps 1-17). Updates x in place.
  * Optional outputs for the tests: V (fp64 vectors), Vh (decoded), Hout (before rotations). */
 static int run_cycle(cycle_ws* ws, const double* r, double beta, double* x, int64_t* iters,
@@ -439,7 +459,7 @@ static int run_cycle(cycle_ws* ws, const double* r, double beta, double* x, int6
       c = 1.0;
       s = 0.0;
     } else {
-      double rr = hypot(a, bb);
+      double rr = givens_radius(a, bb);
       c = a / rr;
       s = bb / rr;
       Rj[j] = rr;
@@ -587,6 +607,8 @@ int orc_gmres(int32_t n, const int32_t* row_ptr, const int32_t* col, const doubl
   int64_t iters = 0, reorths = 0;
   int32_t breakdowns = 0;
   double implicit = 0.0;
+  double cycle_start_rrn = 0.0;
+  int broke_down = 0; /* the last cycle ended on the breakdown test */
   for (;;) {
     /* Step 1 (and the stopping test of step 18, Eq. 4): explicit residual. */
     residual(&ws, b, x, r);
@@ -597,8 +619,15 @@ int orc_gmres(int32_t n, const int32_t* row_ptr, const int32_t* col, const doubl
       res->converged = 1;
       break;
     }
+    if (broke_down && res->true_rrn >= cycle_start_rrn) { /* R18 */
+      res->stagnated = 1;
+      break;
+    }
     if (iters >= ws.max_iters) break;
+    cycle_start_rrn = res->true_rrn;
+    int32_t breakdowns_before = breakdowns;
     run_cycle(&ws, r, beta, x, &iters, &reorths, &breakdowns, &implicit, hist_implicit, NULL, NULL, NULL);
+    broke_down = breakdowns > breakdowns_before;
     res->restarts += 1;
   }
   res->iters = iters;

@@ -69,9 +69,11 @@ typedef struct {
   int64_t restarts;  /* completed restart cycles */
   int64_t reorths;   /* steps that took the second Gram-Schmidt pass */
   int32_t converged; /* explicit ||b - A x|| <= tol ||b|| reached */
-  int32_t breakdowns;
+  int32_t breakdowns; /* cycles that ended on the breakdown test of step 12 (R10) */
   double true_rrn;     /* last explicitly computed ||b - A x|| / ||b|| */
   double implicit_rrn; /* last |g_{j+1}| / ||b|| of the Givens recurrence */
+  int32_t stagnated;   /* stopped because a cycle that ended on a breakdown (step 12) left the
+                          explicit residual no smaller than at that cycle's start (R18) */
 } orc_gmres_result;
 
 /* Solves A x = b. x holds x0 on entry and the result on exit. Returns -3 when the Jacobi

@@ -20,17 +20,23 @@ FORMATS = {"fp64": FP64, "fp32": FP32, "fp16": FP16, "bf16": BF16, "frsz2": FRSZ
 PRECOND = {"none": 0, "jacobi": 1}
 CYCLE = {"auto": 0, "streamed": 1}
 STATUS = {0: "CBG_OK", -1: "CBG_ERR_INVALID_ARG", -2: "CBG_ERR_CUDA", -3: "CBG_ERR_OOM", -4: "CBG_ERR_NONFINITE",
-          -5: "CBG_ERR_NOT_CONVERGED", -6: "CBG_ERR_TIMEOUT", -7: "CBG_ERR_BAD_MATRIX", -8: "CBG_ERR_STATE"}
+          -5: "CBG_ERR_NOT_CONVERGED", -6: "CBG_ERR_TIMEOUT", -7: "CBG_ERR_BAD_MATRIX", -8: "CBG_ERR_STATE",
+          -9: "CBG_ERR_BREAKDOWN_NOT_CONVERGED", -10: "CBG_ERR_UNIMPLEMENTED"}
 ERR_NOT_CONVERGED = -5
+ERR_BREAKDOWN_NOT_CONVERGED = -9
+# statuses with which a solve still writes x and its result
+SOLVE_ENDED = (0, ERR_NOT_CONVERGED, ERR_BREAKDOWN_NOT_CONVERGED)
 
 # Symbols declared in include/cbgmres.h (checked by the CPU tests).
 EXPORTS = ["cbg_frsz2_bytes", "cbg_frsz2_compress", "cbg_frsz2_decompress", "cbg_basis_layout", "cbg_basis_store",
+           "cbg_basis_append",
            "cbg_basis_load", "cbg_basis_work_bytes", "cbg_basis_dot", "cbg_basis_dot_noalloc", "cbg_basis_update", "cbg_intensity",
            "cbg_csr_validate",
            "cbg_spmv_work_bytes", "cbg_spmv", "cbg_opts_default", "cbgmres_workspace_bytes", "cbgmres_create",
            "cbgmres_solve", "cbgmres_start", "cbgmres_advance", "cbgmres_finish", "cbgmres_history",
            "cbgmres_destroy", "cbgmres_basis_vector", "cbgmres_cycle_cluster", "cbg_server_create", "cbg_server_submit", "cbg_server_poll", "cbg_server_stats",
-           "cbg_server_clock", "cbg_server_destroy", "cbg_last_error", "cbg_version"]
+           "cbg_server_clock", "cbg_server_destroy", "cbg_last_error", "cbg_version", "cbgmres_last_error",
+           "frsz2_bytes", "frsz2_compress", "frsz2_decompress"]
 
 
 class CbgError(RuntimeError):
@@ -48,7 +54,7 @@ class Opts(ctypes.Structure):
 class Result(ctypes.Structure):
     _fields_ = [("iters", ctypes.c_int64), ("restarts", ctypes.c_int64), ("reorths", ctypes.c_int64),
                 ("converged", ctypes.c_int32), ("status", ctypes.c_int32), ("true_rrn", ctypes.c_double),
-                ("implicit_rrn", ctypes.c_double), ("seconds", ctypes.c_double)]
+                ("implicit_rrn", ctypes.c_double), ("seconds", ctypes.c_double), ("breakdowns", ctypes.c_int64)]
 
 
 class Request(ctypes.Structure):
@@ -96,6 +102,7 @@ def load(path: str | None = None):
         "cbg_frsz2_decompress": (c_int, [P, P, i64, i32, P, P]),
         "cbg_basis_layout": (c_int, [i64, i32, i32, ctypes.POINTER(i64), ctypes.POINTER(i64)]),
         "cbg_basis_store": (c_int, [ctypes.POINTER(Basis), i32, P, P]),
+        "cbg_basis_append": (c_int, [ctypes.POINTER(Basis), i32, P, P, P, P]),
         "cbg_basis_load": (c_int, [ctypes.POINTER(Basis), i32, P, P]),
         "cbg_basis_work_bytes": (sz, [i64, i32]),
         "cbg_basis_dot": (c_int, [ctypes.POINTER(Basis), i32, P, P, P, sz, P]),
@@ -124,7 +131,11 @@ def load(path: str | None = None):
         "cbg_server_clock": (ctypes.c_double, [P]),
         "cbg_server_destroy": (c_int, [P]),
         "cbg_last_error": (ctypes.c_char_p, []),
+        "cbgmres_last_error": (ctypes.c_char_p, []),
         "cbg_version": (ctypes.c_char_p, []),
+        "frsz2_bytes": (sz, [i64, i32]),
+        "frsz2_compress": (c_int, [P, i64, i32, P, P, P]),
+        "frsz2_decompress": (c_int, [P, P, i64, i32, P, P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -223,6 +234,12 @@ class BasisStorage:
     def store(self, slot: int, x: torch.Tensor, stream=None):
         check(lib().cbg_basis_store(ctypes.byref(self.struct), slot, _ptr(x), _stream(stream)))
 
+    def append(self, slot: int, w: torch.Tensor, h: torch.Tensor, v: torch.Tensor | None = None, stream=None):
+        """v := w / h (h: one positive float64 on the device) stored as vector `slot`; v, when given,
+        receives the FP64 quotient (cbg_basis_append)."""
+        check(lib().cbg_basis_append(ctypes.byref(self.struct), slot, _ptr(w), _ptr(h), _ptr(v), _stream(stream)))
+        return v
+
     def load(self, slot: int, out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
         if out is None:
             out = torch.empty(max(self.n, 1), dtype=torch.float64, device=self.vals.device)
@@ -318,11 +335,12 @@ class SolveResult:
     true_rrn: float
     implicit_rrn: float
     seconds: float
+    breakdowns: int
 
 
 def _result(r: Result) -> SolveResult:
     return SolveResult(r.iters, r.restarts, r.reorths, bool(r.converged), r.status, r.true_rrn, r.implicit_rrn,
-                       r.seconds)
+                       r.seconds, r.breakdowns)
 
 
 class Solver:
@@ -341,7 +359,7 @@ class Solver:
 
     def solve(self, b: torch.Tensor, x: torch.Tensor) -> SolveResult:
         r = Result()
-        check(lib().cbgmres_solve(self.handle, _ptr(b), _ptr(x), ctypes.byref(r)), allow=(0, ERR_NOT_CONVERGED))
+        check(lib().cbgmres_solve(self.handle, _ptr(b), _ptr(x), ctypes.byref(r)), allow=SOLVE_ENDED)
         return _result(r)
 
     def start(self, b: torch.Tensor, x: torch.Tensor):
@@ -350,12 +368,12 @@ class Solver:
 
     def advance(self, max_steps: int) -> bool:
         done = ctypes.c_int32(0)
-        check(lib().cbgmres_advance(self.handle, max_steps, ctypes.byref(done)), allow=(0, ERR_NOT_CONVERGED))
+        check(lib().cbgmres_advance(self.handle, max_steps, ctypes.byref(done)), allow=SOLVE_ENDED)
         return bool(done.value)
 
     def finish(self) -> SolveResult:
         r = Result()
-        check(lib().cbgmres_finish(self.handle, ctypes.byref(r)), allow=(0, ERR_NOT_CONVERGED))
+        check(lib().cbgmres_finish(self.handle, ctypes.byref(r)), allow=SOLVE_ENDED)
         return _result(r)
 
     def history(self, cap: int | None = None):

@@ -85,6 +85,22 @@ int bad(const char* msg) {
 
 bool valid_l(int32_t l) { return l == 16 || l == 21 || l == 32; }
 
+}  // namespace
+
+// CBG_OK for an implemented FRSZ2 code width; CBG_ERR_UNIMPLEMENTED for another width the format
+// admits (2..32 bits); CBG_ERR_INVALID_ARG otherwise.
+int cbg::l_status(int32_t l, const char* what) {
+  if (valid_l(l)) return CBG_OK;
+  if (l >= 2 && l <= 32) {
+    set_error("%s: FRSZ2 code width %d is not implemented (16, 21 or 32)", what, l);
+    return CBG_ERR_UNIMPLEMENTED;
+  }
+  set_error("%s: FRSZ2 code width %d outside [2, 32]", what, l);
+  return CBG_ERR_INVALID_ARG;
+}
+
+namespace {
+
 int value_bytes(int32_t fmt) {
   switch (fmt) {
     case CBG_FP64: return 8;
@@ -95,10 +111,17 @@ int value_bytes(int32_t fmt) {
   }
 }
 
+}  // namespace
+
+namespace cbg {
+
 int check_basis(const cbg_basis* b, int32_t nvec_hi) {
   if (!b) return bad("null basis");
   if (b->fmt < CBG_FP64 || b->fmt > CBG_FRSZ2) return bad("basis: unknown format");
-  if (b->fmt == CBG_FRSZ2 && !valid_l(b->frsz2_bits)) return bad("basis: FRSZ2 code width must be 16, 21 or 32");
+  if (b->fmt == CBG_FRSZ2) {
+    const int st = l_status(b->frsz2_bits, "basis");
+    if (st) return st;
+  }
   if (b->n < 0 || b->n > (int64_t(1) << 40)) return bad("basis: n out of range");
   if (nvec_hi < 0 || nvec_hi > kMaxVecs) return bad("basis: vector index or count out of range (at most 1025)");
   if (b->n == 0) return CBG_OK;
@@ -137,6 +160,10 @@ BasisMut mut(const cbg_basis* b) {
   return v;
 }
 
+}  // namespace cbg
+
+namespace {
+
 // Work buffer of the standalone reducing calls: partial sums, then one 256-byte control region
 // (arrive_last ticket, error word).
 struct Work {
@@ -169,6 +196,22 @@ extern "C" {
 
 const char* cbg_last_error(void) { return g_last_error; }
 
+const char* cbgmres_last_error(void) { return g_last_error; }
+
+size_t frsz2_bytes(int64_t n, int32_t l) {
+  const int64_t b = cbg_frsz2_bytes(n, l);
+  return b < 0 ? 0 : static_cast<size_t>(b);
+}
+
+int frsz2_compress(const double* d_src, int64_t n, int32_t l, uint32_t* d_exp, uint32_t* d_codes, void* stream) {
+  return cbg_frsz2_compress(d_src, n, l, d_exp, d_codes, stream);
+}
+
+int frsz2_decompress(const uint32_t* d_exp, const uint32_t* d_codes, int64_t n, int32_t l, double* d_dst,
+                     void* stream) {
+  return cbg_frsz2_decompress(d_exp, d_codes, n, l, d_dst, stream);
+}
+
 const char* cbg_version(void) { return "cbgmres-gb300 0.1 (sm_103a)"; }
 
 int64_t cbg_frsz2_bytes(int64_t n, int32_t l) {
@@ -178,7 +221,7 @@ int64_t cbg_frsz2_bytes(int64_t n, int32_t l) {
 }
 
 int cbg_frsz2_compress(const double* d_src, int64_t n, int32_t l, uint32_t* d_exps, uint32_t* d_codes, void* stream) {
-  if (!valid_l(l)) return bad("cbg_frsz2_compress: l must be 16, 21 or 32");
+  if (const int lst = l_status(l, "cbg_frsz2_compress")) return lst;
   if (n < 0) return bad("cbg_frsz2_compress: negative n");
   if (n == 0) return CBG_OK;
   if (!d_src || !d_exps || !d_codes) return bad("cbg_frsz2_compress: null pointer");
@@ -192,7 +235,7 @@ int cbg_frsz2_compress(const double* d_src, int64_t n, int32_t l, uint32_t* d_ex
 
 int cbg_frsz2_decompress(const uint32_t* d_exps, const uint32_t* d_codes, int64_t n, int32_t l, double* d_dst,
                          void* stream) {
-  if (!valid_l(l)) return bad("cbg_frsz2_decompress: l must be 16, 21 or 32");
+  if (const int lst = l_status(l, "cbg_frsz2_decompress")) return lst;
   if (n < 0) return bad("cbg_frsz2_decompress: negative n");
   if (n == 0) return CBG_OK;
   if (!d_exps || !d_codes || !d_dst) return bad("cbg_frsz2_decompress: null pointer");
@@ -230,7 +273,22 @@ int cbg_basis_store(const cbg_basis* basis, int32_t slot, const double* d_src, v
   DeviceInfo di;
   st = device_info(&di);
   if (st) return st;
-  return launch_store(mut(basis), slot, d_src, nullptr, nullptr, nullptr, Gate{nullptr, nullptr},
+  return launch_store(mut(basis), slot, d_src, nullptr, nullptr, nullptr, nullptr, Gate{nullptr, nullptr},
+                      static_cast<cudaStream_t>(stream));
+}
+
+int cbg_basis_append(const cbg_basis* basis, int32_t slot, const double* d_w, const double* d_h, double* d_v,
+                     void* stream) {
+  int st = check_basis(basis, slot + 1);
+  if (st) return st;
+  if (slot < 0) return bad("cbg_basis_append: negative slot");
+  if (basis->n == 0) return CBG_OK;
+  if (!d_w || !aligned(d_w, 8) || !d_h || !aligned(d_h, 8) || (d_v && !aligned(d_v, 8)))
+    return bad("cbg_basis_append: bad w, h or v pointer");
+  DeviceInfo di;
+  st = device_info(&di);
+  if (st) return st;
+  return launch_store(mut(basis), slot, d_w, d_h, nullptr, d_v, nullptr, Gate{nullptr, nullptr},
                       static_cast<cudaStream_t>(stream));
 }
 

@@ -30,13 +30,34 @@ __device__ __forceinline__ bool gate_skip_c(const Gate& g) {
 
 }  // namespace
 
+// The divisor of the normalisation v := w / h (Fig. 1 steps 1 and 13) and RN(1/h): read from the
+// device when given (the solver computes 1/h once per step), else 1/h by one IEEE division per CTA.
+__device__ __forceinline__ void divisor(const double* hdiv_ptr, const double* rcp_ptr, double* h, double* rcp) {
+  __shared__ double s_rcp;
+  if (!hdiv_ptr) {
+    *h = 1.0;
+    *rcp = 1.0;
+    return;
+  }
+  *h = *hdiv_ptr;
+  if (rcp_ptr) {
+    *rcp = *rcp_ptr;
+    return;
+  }
+  if (threadIdx.x == 0) s_rcp = 1.0 / *h;
+  __syncthreads();
+  *rcp = s_rcp;
+}
+
 template <int L, int U>
 __global__ void __launch_bounds__(256) k_frsz2_compress(const double* __restrict__ src, int64_t n,
                                                         uint32_t* __restrict__ exps, uint32_t* __restrict__ codes,
+                                                        const double* __restrict__ hdiv_ptr,
                                                         const double* __restrict__ rcp_ptr, double* __restrict__ vout,
                                                         const double* __restrict__ dscale, Gate gate) {
   if (gate_skip_c(gate)) return;
-  const double rcp = rcp_ptr ? *rcp_ptr : 1.0;
+  double hdiv, rcp;
+  divisor(hdiv_ptr, rcp_ptr, &hdiv, &rcp);
   const int lane = threadIdx.x & 31;
   const int64_t nb = (n + 31) / 32;
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -54,9 +75,9 @@ __global__ void __launch_bounds__(256) k_frsz2_compress(const double* __restrict
       if (b >= nb) break;  // uniform across the warp
       const int64_t k = b * 32 + lane;
       double v = x[u];
-      if (rcp_ptr) {
-        v = v * rcp;  // v := w / h as w * (1/h)
-        if (k < n) vout[k] = dscale ? v * dscale[k] : v;  // the SpMV input M^{-1} v (Fig. 1 step 3)
+      if (hdiv_ptr) {
+        v = div_rn(v, hdiv, rcp);  // v := w / h, correctly rounded
+        if (k < n && vout) vout[k] = dscale ? v * dscale[k] : v;  // the SpMV input M^{-1} v (Fig. 1 step 3)
       }
       const uint64_t bits = static_cast<uint64_t>(__double_as_longlong(v));
       // step 1: block maximum of the exponent fields
@@ -98,16 +119,17 @@ __global__ void k_frsz2_decompress(const uint32_t* __restrict__ exps, const uint
 // Cast storage: round to nearest even directly from FP64 with CUDA's conversion intrinsics.
 template <int F>
 __global__ void k_cast_store(const double* __restrict__ src, int64_t n, uint8_t* __restrict__ dst,
-                             const double* __restrict__ rcp_ptr, double* __restrict__ vout,
-                             const double* __restrict__ dscale, Gate gate) {
+                             const double* __restrict__ hdiv_ptr, const double* __restrict__ rcp_ptr,
+                             double* __restrict__ vout, const double* __restrict__ dscale, Gate gate) {
   if (gate_skip_c(gate)) return;
-  const double rcp = rcp_ptr ? *rcp_ptr : 1.0;
+  double hdiv, rcp;
+  divisor(hdiv_ptr, rcp_ptr, &hdiv, &rcp);
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += stride) {
     double v = src[k];
-    if (rcp_ptr) {
-      v = v * rcp;
-      vout[k] = dscale ? v * dscale[k] : v;
+    if (hdiv_ptr) {
+      v = div_rn(v, hdiv, rcp);  // v := w / h, correctly rounded
+      if (vout) vout[k] = dscale ? v * dscale[k] : v;
     }
     if (F == CBG_FP64) {
       reinterpret_cast<double*>(dst)[k] = v;
@@ -153,23 +175,24 @@ int check_launch(const char* what) {
 }  // namespace
 
 int launch_frsz2_compress_impl(const double* src, int64_t n, int l, uint32_t* exps, uint32_t* codes,
-                               const double* rcp, double* vout, const double* dscale, const Gate& gate,
-                               cudaStream_t stream) {
+                               const double* hdiv, const double* rcp, double* vout, const double* dscale,
+                               const Gate& gate, cudaStream_t stream) {
   if (n <= 0) return CBG_OK;
   constexpr int U = 4;
   const int64_t nb = (n + 31) / 32;
   const int grid = grid_elems((nb + U - 1) / U * 32, 256, 16);
   switch (l) {
-    case 32: k_frsz2_compress<32, U><<<grid, 256, 0, stream>>>(src, n, exps, codes, rcp, vout, dscale, gate); break;
-    case 21: k_frsz2_compress<21, U><<<grid, 256, 0, stream>>>(src, n, exps, codes, rcp, vout, dscale, gate); break;
-    case 16: k_frsz2_compress<16, U><<<grid, 256, 0, stream>>>(src, n, exps, codes, rcp, vout, dscale, gate); break;
+    case 32: k_frsz2_compress<32, U><<<grid, 256, 0, stream>>>(src, n, exps, codes, hdiv, rcp, vout, dscale, gate); break;
+    case 21: k_frsz2_compress<21, U><<<grid, 256, 0, stream>>>(src, n, exps, codes, hdiv, rcp, vout, dscale, gate); break;
+    case 16: k_frsz2_compress<16, U><<<grid, 256, 0, stream>>>(src, n, exps, codes, hdiv, rcp, vout, dscale, gate); break;
     default: return CBG_ERR_INVALID_ARG;
   }
   return check_launch("frsz2 compress launch");
 }
 
 int launch_frsz2_compress(const double* src, int64_t n, int l, uint32_t* exps, uint32_t* codes, cudaStream_t stream) {
-  return launch_frsz2_compress_impl(src, n, l, exps, codes, nullptr, nullptr, nullptr, Gate{nullptr, nullptr}, stream);
+  return launch_frsz2_compress_impl(src, n, l, exps, codes, nullptr, nullptr, nullptr, nullptr, Gate{nullptr, nullptr},
+                                    stream);
 }
 
 int launch_frsz2_decompress(const uint32_t* exps, const uint32_t* codes, int64_t n, int l, double* dst,
@@ -185,21 +208,21 @@ int launch_frsz2_decompress(const uint32_t* exps, const uint32_t* codes, int64_t
   return check_launch("frsz2 decompress launch");
 }
 
-int launch_store(const BasisMut& B, int slot, const double* src, const double* rcp, double* vout,
+int launch_store(const BasisMut& B, int slot, const double* src, const double* hdiv, const double* rcp, double* vout,
                  const double* dscale, const Gate& gate, cudaStream_t stream) {
   if (B.n <= 0) return CBG_OK;
   uint8_t* vals = B.vals + (int64_t)slot * B.vstride;
   if (B.fmt == CBG_FRSZ2) {
     uint32_t* exps = reinterpret_cast<uint32_t*>(reinterpret_cast<uint8_t*>(B.exps) + (int64_t)slot * B.estride);
-    return launch_frsz2_compress_impl(src, B.n, B.l, exps, reinterpret_cast<uint32_t*>(vals), rcp, vout, dscale, gate,
-                                      stream);
+    return launch_frsz2_compress_impl(src, B.n, B.l, exps, reinterpret_cast<uint32_t*>(vals), hdiv, rcp, vout, dscale,
+                                      gate, stream);
   }
   const int grid = grid_elems(B.n, 256, 16);
   switch (B.fmt) {
-    case CBG_FP64: k_cast_store<CBG_FP64><<<grid, 256, 0, stream>>>(src, B.n, vals, rcp, vout, dscale, gate); break;
-    case CBG_FP32: k_cast_store<CBG_FP32><<<grid, 256, 0, stream>>>(src, B.n, vals, rcp, vout, dscale, gate); break;
-    case CBG_FP16: k_cast_store<CBG_FP16><<<grid, 256, 0, stream>>>(src, B.n, vals, rcp, vout, dscale, gate); break;
-    case CBG_BF16: k_cast_store<CBG_BF16><<<grid, 256, 0, stream>>>(src, B.n, vals, rcp, vout, dscale, gate); break;
+    case CBG_FP64: k_cast_store<CBG_FP64><<<grid, 256, 0, stream>>>(src, B.n, vals, hdiv, rcp, vout, dscale, gate); break;
+    case CBG_FP32: k_cast_store<CBG_FP32><<<grid, 256, 0, stream>>>(src, B.n, vals, hdiv, rcp, vout, dscale, gate); break;
+    case CBG_FP16: k_cast_store<CBG_FP16><<<grid, 256, 0, stream>>>(src, B.n, vals, hdiv, rcp, vout, dscale, gate); break;
+    case CBG_BF16: k_cast_store<CBG_BF16><<<grid, 256, 0, stream>>>(src, B.n, vals, hdiv, rcp, vout, dscale, gate); break;
     default: return CBG_ERR_INVALID_ARG;
   }
   return check_launch("cast store launch");

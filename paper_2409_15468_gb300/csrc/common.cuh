@@ -59,6 +59,58 @@ __device__ __forceinline__ double fma_pow2(double v, int x, double acc) {
   return acc + scale_pow2(v, x);
 }
 
+// The correctly rounded quotient w / h (round to nearest even, as IEEE division) for a divisor
+// h > 0, given rcp = RN(1/h), at the cost of one FP64 multiply and integer arithmetic. (For h = 0
+// the caller passes rcp = 0 and gets w * 0.)
+//
+// q = RN(w * rcp) lies within 1.5 units in the last place of w / h, so RN(w / h) is q or one of
+// its neighbours. With the integer significands (53 bits, hidden bit explicit) w = mw 2^(ew-1075),
+// h = mh 2^(eh-1075) and q = mq 2^(eq-1075), the remainder in units of 2^(eq+eh-2150),
+//   R = mw 2^(ew+1075-eq-eh) - mq mh,
+// is exact in 64-bit integers (|R| < 2^56 for such a q), and (w/h - q) / ulp(q) = R / mh. So q is
+// the rounded quotient exactly when -1/2 (-1/4 below a power of two, where the next double down
+// is half an ulp away) < R / mh < 1/2; otherwise the neighbour in the direction of R's sign is
+// tested the same way. Exact halfway quotients of two 53-bit significands do not exist, so no tie
+// arises. Zero, subnormal or non-finite operands, a quotient outside the normal range, and a
+// candidate that fails both tests (not expected) take the IEEE division.
+__device__ __forceinline__ double div_rn(double w, double h, double rcp) {
+  const double q0 = w * rcp;
+  const uint64_t uw = static_cast<uint64_t>(__double_as_longlong(w));
+  const uint64_t uh = static_cast<uint64_t>(__double_as_longlong(h));
+  const uint64_t uq0 = static_cast<uint64_t>(__double_as_longlong(q0));
+  const int ew = static_cast<int>((uw >> 52) & 0x7FF), eh = static_cast<int>((uh >> 52) & 0x7FF);
+  const int eq0 = static_cast<int>((uq0 >> 52) & 0x7FF);
+  if (ew == 0 || ew == 0x7FF || eh == 0 || eh == 0x7FF || eq0 <= 1 || eq0 >= 0x7FE) {
+    if (w == 0.0 || !(h > 0.0)) return q0;  // +-0 / h = +-0; a zero divisor (rcp 0) keeps w * rcp
+    return w / h;
+  }
+  constexpr uint64_t kHidden = 1ull << 52, kMant = kHidden - 1;
+  const uint64_t mw = (uw & kMant) | kHidden, mh = (uh & kMant) | kHidden;
+  const uint64_t sgn = uw & (1ull << 63);
+  // true when the magnitude with bits `uq` is RN(|w| / h); *up receives the sign of R
+  auto rounded = [&](uint64_t uq, bool* up) {
+    const int eq = static_cast<int>(uq >> 52);
+    const uint64_t mq = (uq & kMant) | kHidden;
+    const int s = ew + 1075 - eq - eh;
+    if (s < 0 || s > 63) {
+      *up = s > 63;
+      return false;
+    }
+    const long long R = static_cast<long long>((mw << s) - mq * mh);
+    *up = R > 0;
+    if (R >= 0) return static_cast<uint64_t>(2 * R) < mh;
+    const uint64_t a = static_cast<uint64_t>(-R);
+    return (mq == kHidden ? 4 * a : 2 * a) < mh;
+  };
+  const uint64_t m0 = uq0 & ~(1ull << 63);
+  bool up = false;
+  if (rounded(m0, &up)) return __longlong_as_double(static_cast<long long>(m0 | sgn));
+  const uint64_t m1 = up ? m0 + 1 : m0 - 1;  // the next double up or down in magnitude
+  bool up1 = false;
+  if (rounded(m1, &up1)) return __longlong_as_double(static_cast<long long>(m1 | sgn));
+  return w / h;
+}
+
 // ---- mbarrier and bulk-copy (TMA) wrappers ---------------------------------------------------
 
 __device__ __forceinline__ uint32_t smem_addr(const void* p) {
@@ -182,7 +234,8 @@ struct SolverCtl {
   double beta;       // ||r0|| at the start of the cycle
   double bnorm;      // ||b||
   double tol;        // target relative residual (Eq. 4)
-  double rcp;        // 1 / (norm used for the next normalisation)
+  double hdiv;       // the norm the next normalisation divides by (step 1: beta; step 13: h_{j+1,j})
+  double rcp;        // RN(1 / hdiv)
   double implicit;   // |g_{j+1}| / ||b||
   double eta;
   unsigned int counters[8];  // arrive_last tickets, one per kernel kind

@@ -46,12 +46,24 @@ __device__ __forceinline__ void norm_epilogue(const NormEpilogue& e, double norm
       break;
     case kEpiResidual:  // step 1: beta = ||r0||, v = r0 / beta
       c->beta = nrm;
+      c->hdiv = nrm;
       c->rcp = nrm > 0.0 ? 1.0 / nrm : 0.0;
       break;
     default:
       break;
   }
 }
+
+// ---- capi.cu: argument checks shared by the C entry points ----------------------------------
+// CBG_OK when `b` describes a basis the fused kernels can read for vector indices below nvec_hi
+// (format, code width, n, 256-byte aligned pointers and strides from cbg_basis_layout); the
+// CBG_ERR_* status otherwise, with the message set.
+int check_basis(const cbg_basis* b, int32_t nvec_hi);
+BasisView view(const cbg_basis* b);
+BasisMut mut(const cbg_basis* b);
+// CBG_OK for FRSZ2 code widths 16, 21, 32; CBG_ERR_UNIMPLEMENTED for another width in [2, 32];
+// CBG_ERR_INVALID_ARG otherwise (message set, prefixed with `what`).
+int l_status(int32_t l, const char* what);
 
 // ---- basis.cu / basis_frsz2.cu -----------------------------------------------------------------
 // Grid for a reducing basis kernel: occupancy x SMs, at most one CTA per units_per_cta_min units,
@@ -79,10 +91,11 @@ int launch_basis_update(const BasisView& B, int nvec, const int* nvec_dev, const
                         const Gate& gate, cudaStream_t stream);
 
 // ---- codec.cu -----------------------------------------------------------------------------------
-// Stores src (times *rcp when rcp is not null) into basis vector `slot`; with rcp, the scaled
-// vector is also written to vout, multiplied elementwise by dscale when dscale is not null (the
-// SpMV input M^{-1} v of a right preconditioner M = diag^{-1}(dscale)).
-int launch_store(const BasisMut& B, int slot, const double* src, const double* rcp, double* vout,
+// Stores src into basis vector `slot`; when hdiv is not null, stores v = src / *hdiv instead
+// (correctly rounded; *rcp = RN(1 / *hdiv) when rcp is not null, else computed), and writes v to
+// vout when vout is not null, multiplied elementwise by dscale when dscale is not null (the SpMV
+// input M^{-1} v of a right preconditioner M = diag^{-1}(dscale)).
+int launch_store(const BasisMut& B, int slot, const double* src, const double* hdiv, const double* rcp, double* vout,
                  const double* dscale, const Gate& gate, cudaStream_t stream);
 int launch_frsz2_compress(const double* src, int64_t n, int l, uint32_t* exps, uint32_t* codes, cudaStream_t stream);
 int launch_frsz2_decompress(const uint32_t* exps, const uint32_t* codes, int64_t n, int l, double* dst,
@@ -125,6 +138,21 @@ struct GivensArgs {
 };
 int launch_givens(const GivensArgs& a, int j, cudaStream_t stream);
 int launch_cycle_init(SolverCtl* ctl, double* g, int m, int steps_allowed, cudaStream_t stream);
+
+// The length r = sqrt(a*a + b*b) of the Givens rotation that zeroes b against a (Fig. 1 step 17),
+// as IEEE operations in that order (no fused multiply-add), after an exact power-of-two scaling when
+// the larger exponent field is above 1523 or below 523. The oracle evaluates the same expression,
+// so both round r identically; it is also cheaper than a library hypot on GB300 (one square root
+// and two dependent FP64 operations against ~1 000 cycles).
+__device__ __forceinline__ double givens_radius(double a, double b) {
+  const int ea = static_cast<int>((static_cast<unsigned long long>(__double_as_longlong(a)) >> 52) & 0x7FF);
+  const int eb = static_cast<int>((static_cast<unsigned long long>(__double_as_longlong(b)) >> 52) & 0x7FF);
+  const int e = ea > eb ? ea : eb;
+  if (e <= 1523 && e >= 523) return sqrt(__dadd_rn(__dmul_rn(a, a), __dmul_rn(b, b)));
+  const double scale = e > 1523 ? 0x1p-600 : 0x1p600;
+  const double as = __dmul_rn(a, scale), bs = __dmul_rn(b, scale);
+  return __ddiv_rn(sqrt(__dadd_rn(__dmul_rn(as, as), __dmul_rn(bs, bs))), scale);
+}
 
 // Applies the rotations 0..j-1 of the least-squares update (Fig. 1 step 17) to col[0..j], called
 // by all 32 lanes of one warp: col[i] := c_i x_i + s_i y_i with x_0 = col[0],

@@ -25,12 +25,11 @@ constexpr size_t kControlDoubles = 32;  // 256 bytes: completion counter, error 
 // the address up with cudaGetSymbolAddress.
 static __device__ __align__(256) double g_noalloc_scratch[kPartialDoubles + kControlDoubles];
 
-struct DeviceScratch {
-  std::once_flag once;
-  double* ptr = nullptr;
-  cudaError_t status = cudaSuccess;
-};
-DeviceScratch g_scratch[64];
+// Device address of the scratch array per device index, looked up once with that device current.
+// A failed lookup (for example one attempted during a stream capture) is not remembered: the next
+// call tries again.
+std::mutex g_scratch_mu;
+double* g_scratch_ptr[64] = {};
 
 }  // namespace
 
@@ -38,38 +37,30 @@ using namespace cbg;
 
 extern "C" int cbg_basis_dot_noalloc(const cbg_basis* b, int32_t nvec, const double* d_w, double* d_h,
                                      void* stream) {
-  if (!b) {
-    set_error("cbg_basis_dot_noalloc: null basis");
-    return CBG_ERR_INVALID_ARG;
-  }
-  if (nvec < 0 || nvec > kNoAllocMaxVecs) {
-    set_error("cbg_basis_dot_noalloc: nvec = %d is outside [0, %d], the capacity of its fixed scratch array "
+  int st = check_basis(b, nvec);
+  if (st) return st;
+  if (nvec > kNoAllocMaxVecs) {
+    set_error("cbg_basis_dot_noalloc: nvec = %d is above %d, the capacity of its fixed scratch array "
               "(use cbg_basis_dot with a caller-provided work buffer for more vectors)",
               nvec, kNoAllocMaxVecs);
     return CBG_ERR_INVALID_ARG;
   }
-  if (b->fmt < CBG_FP64 || b->fmt > CBG_FRSZ2 ||
-      (b->fmt == CBG_FRSZ2 && b->frsz2_bits != 16 && b->frsz2_bits != 21 && b->frsz2_bits != 32) || b->n < 0 ||
-      b->n > (int64_t(1) << 40)) {
-    set_error("cbg_basis_dot_noalloc: bad basis format, code width or n");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (nvec == 0) return CBG_OK;
+  if (!d_h || reinterpret_cast<uintptr_t>(d_h) % 8) {
+    set_error("cbg_basis_dot_noalloc: bad h pointer");
     return CBG_ERR_INVALID_ARG;
   }
-  if (nvec == 0 || b->n == 0) return CBG_OK;
-  int64_t vs = 0, es = 0;
-  cbg_basis_layout(b->n, b->fmt, b->fmt == CBG_FRSZ2 ? b->frsz2_bits : 32, &vs, &es);
-  const bool frsz2 = b->fmt == CBG_FRSZ2;
-  if (!b->vals || reinterpret_cast<uintptr_t>(b->vals) % 256 || b->vals_stride < vs || b->vals_stride % 256 ||
-      (frsz2 && (!b->exps || reinterpret_cast<uintptr_t>(b->exps) % 256 || b->exps_stride < es ||
-                 b->exps_stride % 256))) {
-    set_error("cbg_basis_dot_noalloc: basis pointers must be 256-byte aligned with strides from cbg_basis_layout");
-    return CBG_ERR_INVALID_ARG;
+  if (b->n == 0) {  // the empty sums
+    cudaError_t e = cudaMemsetAsync(d_h, 0, sizeof(double) * nvec, s);
+    return e == cudaSuccess ? CBG_OK : cuda_fail(e, "cbg_basis_dot_noalloc: zero fill");
   }
-  if (!d_w || !d_h || reinterpret_cast<uintptr_t>(d_w) % 16 || reinterpret_cast<uintptr_t>(d_h) % 8) {
-    set_error("cbg_basis_dot_noalloc: bad w or h pointer");
+  if (!d_w || reinterpret_cast<uintptr_t>(d_w) % 16) {
+    set_error("cbg_basis_dot_noalloc: bad w pointer");
     return CBG_ERR_INVALID_ARG;
   }
   DeviceInfo di;
-  int st = device_info(&di);
+  st = device_info(&di);
   if (st) return st;
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
@@ -78,29 +69,27 @@ extern "C" int cbg_basis_dot_noalloc(const cbg_basis* b, int32_t nvec, const dou
     set_error("cbg_basis_dot_noalloc: device index %d out of range", dev);
     return CBG_ERR_CUDA;
   }
-  // One-time set-up per device, with that device current: the device address of the scratch array.
-  DeviceScratch& ds = g_scratch[dev];
-  std::call_once(ds.once, [&]() {
-    void* p = nullptr;
-    ds.status = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-    ds.ptr = static_cast<double*>(p);
-  });
-  if (ds.status != cudaSuccess || !ds.ptr) return cuda_fail(ds.status, "cbg_basis_dot_noalloc: cudaGetSymbolAddress");
-
-  cudaStream_t s = static_cast<cudaStream_t>(stream);
-  double* partials = ds.ptr;
-  double* control = ds.ptr + kPartialDoubles;
+  // Set-up per device, with that device current: the device address of the scratch array (the
+  // array's name is only a host-side stand-in in host code).
+  double* base = nullptr;
+  {
+    std::lock_guard<std::mutex> lk(g_scratch_mu);
+    if (!g_scratch_ptr[dev]) {
+      void* p = nullptr;
+      e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+      if (e != cudaSuccess || !p) {
+        cudaGetLastError();
+        return cuda_fail(e != cudaSuccess ? e : cudaErrorInvalidSymbol, "cbg_basis_dot_noalloc: cudaGetSymbolAddress");
+      }
+      g_scratch_ptr[dev] = static_cast<double*>(p);
+    }
+    base = g_scratch_ptr[dev];
+  }
+  double* partials = base;
+  double* control = base + kPartialDoubles;
   // The completion counter must start at zero; the array keeps whatever the previous call left.
   e = cudaMemsetAsync(control, 0, kControlDoubles * sizeof(double), s);
   if (e != cudaSuccess) return cuda_fail(e, "cbg_basis_dot_noalloc: control reset");
-  BasisView v;
-  v.vals = static_cast<const uint8_t*>(b->vals);
-  v.vstride = b->vals_stride;
-  v.exps = b->exps;
-  v.estride = b->exps_stride;
-  v.n = b->n;
-  v.fmt = b->fmt;
-  v.l = frsz2 ? b->frsz2_bits : 32;
-  return launch_basis_dot_capped(v, nvec, d_w, d_h, partials, reinterpret_cast<unsigned int*>(control),
+  return launch_basis_dot_capped(view(b), nvec, d_w, d_h, partials, reinterpret_cast<unsigned int*>(control),
                                  reinterpret_cast<int*>(control) + 4, kNoAllocMaxGrid, s);
 }

@@ -203,12 +203,13 @@ __global__ void __launch_bounds__(kOcThreads, 1) k_cycle_onchip(OnchipArgs a, Oc
     __syncthreads();
   };
 
-  // v := w * rcp into basis slot `slot` (Fig. 1 steps 13-14; step 1 for slot 0) and z := M^{-1} v.
-  auto store = [&](int slot, double rcp) {
+  // v := w / hdiv (correctly rounded; rcp = RN(1 / hdiv)) into basis slot `slot` (Fig. 1 steps
+  // 13-14; step 1 for slot 0) and z := M^{-1} v.
+  auto store = [&](int slot, double hdiv, double rcp) {
     uint8_t* sb = s.codes + (size_t)slot * lay.slot_bytes;
     for (int b = warp; b < NB; b += kOcWarps) {
       const int i = b * 32 + lane, gi = row0 + i;
-      const double v = gi < n ? s.w[i] * rcp : 0.0;  // rows past n: the padding +0.0
+      const double v = gi < n ? div_rn(s.w[i], hdiv, rcp) : 0.0;  // rows past n: the padding +0.0
       s.z[i] = gi < n ? (a.dinv ? v * a.dinv[gi] : v) : 0.0;
       if (F == CBG_FRSZ2) {
         const uint64_t bits = static_cast<uint64_t>(__double_as_longlong(v));
@@ -486,7 +487,7 @@ __global__ void __launch_bounds__(kOcThreads, 1) k_cycle_onchip(OnchipArgs a, Oc
     S.implicit = ctl->implicit;
   }
   __syncthreads();
-  store(0, S.rcp);
+  store(0, ctl->hdiv, S.rcp);
   cluster_sync();  // every CTA's z is complete
 
   // ---- Arnoldi steps (steps 3-16) ---------------------------------------------------------------
@@ -547,7 +548,7 @@ __global__ void __launch_bounds__(kOcThreads, 1) k_cycle_onchip(OnchipArgs a, Oc
       const bool reorth = S.reorth != 0;
       const double hn = S.hn, hn_first = S.hn_first, xc = S.xc;
       // lane 0 c = x / r, lane 1 s = h / r, lane 2 the next normalisation 1 / h
-      const double r = hypot(xc, hn);
+      const double r = givens_radius(xc, hn);
       const double num = lane == 0 ? xc : (lane == 1 ? hn : 1.0);
       const double den = lane == 2 ? hn : r;
       const double q = (lane < 3 && den != 0.0) ? num / den : 0.0;
@@ -586,7 +587,7 @@ __global__ void __launch_bounds__(kOcThreads, 1) k_cycle_onchip(OnchipArgs a, Oc
       __syncwarp();  // bar.sync is .aligned
       asm volatile("bar.sync 1, %0;" ::"n"(kOcThreads) : "memory");
     }
-    store(j + 1, S.rcp);
+    store(j + 1, S.hn, S.rcp);
     cluster_sync();  // every CTA's z is complete, and S.stop is set
   }
   __syncthreads();
@@ -641,6 +642,7 @@ __global__ void __launch_bounds__(kOcThreads, 1) k_cycle_onchip(OnchipArgs a, Oc
     }
     const double nrm = sqrt(b2);
     ctl->beta = nrm;
+    ctl->hdiv = nrm;
     ctl->rcp = nrm > 0.0 ? 1.0 / nrm : 0.0;
     ctl->stop = S.stop;
     ctl->reorth = 0;

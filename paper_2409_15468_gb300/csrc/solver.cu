@@ -84,7 +84,7 @@ __global__ void __launch_bounds__(32) k_givens(GivensArgs a, int j) {
   const double hn = __shfl_sync(0xffffffffu, sqv, 0), hn_first = __shfl_sync(0xffffffffu, sqv, 1);
   const double x = rotate_column_warp(col, scs, ssn, sp, sq, j, lane), y = hn;
   // the new rotation: lane 0 c = x / r, lane 1 s = y / r, lane 2 the next normalisation 1 / h
-  const double r = hypot(x, y);
+  const double r = givens_radius(x, y);
   const double num = lane == 0 ? x : (lane == 1 ? y : 1.0);
   const double den = lane == 2 ? hn : r;
   const double qv = (lane < 3 && den != 0.0) ? num / den : 0.0;
@@ -111,6 +111,7 @@ __global__ void __launch_bounds__(32) k_givens(GivensArgs a, int j) {
       c->stop = 1;
     }
     if (breakdown || implicit <= c->tol || j + 1 >= c->steps_allowed) c->stop = 1;
+    c->hdiv = hn;
     c->rcp = hn > 0.0 ? rcp : 0.0;
     c->reorth = 0;
   }
@@ -235,7 +236,7 @@ struct cbg_ctx {
   int phase;
   int j;
   int steps_allowed;
-  int64_t iters, restarts, reorths;
+  int64_t iters, restarts, reorths, breakdowns;
   double bnorm, true_rrn, implicit;
   int status, converged, first_residual;
   std::chrono::steady_clock::time_point t0;
@@ -250,18 +251,32 @@ struct Layout {
       off_partials, off_hist, off_ctl, off_bnorm2, off_dinv, off_z, off_perm, off_perm_scratch, total;
 };
 
-bool opts_valid(int32_t n, const cbg_opts* o) {
-  if (!o) return false;
-  if (n < 1) return false;
-  if (o->restart < 1 || o->restart > 1024 || o->restart > n) return false;
-  if (!(o->tol > 0.0) || !std::isfinite(o->tol)) return false;
-  if (o->max_iters < 0) return false;
-  if (!(o->eta >= 0.0) || !std::isfinite(o->eta)) return false;
-  if (o->fmt < CBG_FP64 || o->fmt > CBG_FRSZ2) return false;
-  if (o->fmt == CBG_FRSZ2 && o->frsz2_bits != 16 && o->frsz2_bits != 21 && o->frsz2_bits != 32) return false;
-  if (o->precond != CBG_PRECOND_NONE && o->precond != CBG_PRECOND_JACOBI) return false;
-  if (o->cycle != CBG_CYCLE_AUTO && o->cycle != CBG_CYCLE_STREAMED) return false;
-  return true;
+// CBG_OK, CBG_ERR_UNIMPLEMENTED (an FRSZ2 code width in [2, 32] other than 16, 21 and 32) or
+// CBG_ERR_INVALID_ARG; does not set the error message.
+int opts_status(int32_t n, const cbg_opts* o) {
+  if (!o) return CBG_ERR_INVALID_ARG;
+  if (n < 1) return CBG_ERR_INVALID_ARG;
+  if (o->restart < 1 || o->restart > 1024 || o->restart > n) return CBG_ERR_INVALID_ARG;
+  if (!(o->tol > 0.0) || !std::isfinite(o->tol)) return CBG_ERR_INVALID_ARG;
+  if (o->max_iters < 0) return CBG_ERR_INVALID_ARG;
+  if (!(o->eta >= 0.0) || !std::isfinite(o->eta)) return CBG_ERR_INVALID_ARG;
+  if (o->fmt < CBG_FP64 || o->fmt > CBG_FRSZ2) return CBG_ERR_INVALID_ARG;
+  if (o->precond != CBG_PRECOND_NONE && o->precond != CBG_PRECOND_JACOBI) return CBG_ERR_INVALID_ARG;
+  if (o->cycle != CBG_CYCLE_AUTO && o->cycle != CBG_CYCLE_STREAMED) return CBG_ERR_INVALID_ARG;
+  if (o->fmt == CBG_FRSZ2 && o->frsz2_bits != 16 && o->frsz2_bits != 21 && o->frsz2_bits != 32)
+    return (o->frsz2_bits >= 2 && o->frsz2_bits <= 32) ? CBG_ERR_UNIMPLEMENTED : CBG_ERR_INVALID_ARG;
+  return CBG_OK;
+}
+
+bool opts_valid(int32_t n, const cbg_opts* o) { return opts_status(n, o) == CBG_OK; }
+
+int opts_fail(int32_t n, const cbg_opts* o) {
+  const int st = opts_status(n, o);
+  if (st == CBG_ERR_UNIMPLEMENTED)
+    set_error("cbgmres_create: FRSZ2 code width %d is not implemented (16, 21 or 32)", o->frsz2_bits);
+  else
+    set_error("cbgmres_create: invalid n or options (1 <= restart <= min(n, 1024), tol > 0, l in {16,21,32})");
+  return st;
 }
 
 Layout layout_of(int32_t n, const cbg_opts* o) {
@@ -404,7 +419,7 @@ int enqueue_step(cbg_ctx* c, int j) {
   st = launch_givens(givens_args(c), j, c->stream);
   if (st) return st;
   if (j + 1 <= c->opts.restart) {
-    st = launch_store(c->basis, j + 1, c->w, &ctl->rcp, c->v, c->dinv, run, c->stream);
+    st = launch_store(c->basis, j + 1, c->w, &ctl->hdiv, &ctl->rcp, c->v, c->dinv, run, c->stream);
     if (st) return st;
   }
   return CBG_OK;
@@ -458,6 +473,7 @@ int status_from_err(int err) {
 // The residual of a cycle start is on the host: account the finished cycle and decide what next.
 int after_residual(cbg_ctx* c) {
   const SolverCtl& h = *c->ctl_host;
+  bool broke_down = false;  // the cycle that just ended did so on the breakdown test (step 12)
   if (c->first_residual) {
     c->first_residual = 0;
   } else {
@@ -465,9 +481,12 @@ int after_residual(cbg_ctx* c) {
     c->reorths += h.reorth_count;
     c->restarts += 1;
     c->implicit = h.implicit;
+    broke_down = h.breakdown != 0;
+    if (broke_down) c->breakdowns += 1;
   }
   int st = status_from_err(h.err);
   if (st) return ctx_fail(c, st);
+  const double cycle_start_rrn = c->true_rrn;
   c->true_rrn = c->bnorm > 0.0 ? h.beta / c->bnorm : 0.0;
   if (!std::isfinite(c->true_rrn)) {
     set_error("the residual became NaN or infinite");
@@ -476,6 +495,15 @@ int after_residual(cbg_ctx* c) {
   if (c->true_rrn <= c->opts.tol) {
     c->converged = 1;
     c->status = CBG_OK;
+    c->phase = kDone;
+    return CBG_OK;
+  }
+  // A breakdown that left the residual where the cycle started: the Krylov space stopped growing,
+  // and repeating the cycle would give the same result (the oracle's reading R18).
+  if (broke_down && c->true_rrn >= cycle_start_rrn) {
+    set_error("breakdown (Fig. 1 step 12) without progress: relative residual %.3e at restart %lld",
+              c->true_rrn, static_cast<long long>(c->restarts));
+    c->status = CBG_ERR_BREAKDOWN_NOT_CONVERGED;
     c->phase = kDone;
     return CBG_OK;
   }
@@ -495,7 +523,7 @@ int after_residual(cbg_ctx* c) {
   st = launch_cycle_init(c->ctl, c->g, c->opts.restart, c->steps_allowed, c->stream);
   if (st) return ctx_fail(c, st);
   // v_1 := r0 / beta, stored as basis vector 0 (step 1)
-  st = launch_store(c->basis, 0, c->w, &c->ctl->rcp, c->v, c->dinv, Gate{nullptr, nullptr}, c->stream);
+  st = launch_store(c->basis, 0, c->w, &c->ctl->hdiv, &c->ctl->rcp, c->v, c->dinv, Gate{nullptr, nullptr}, c->stream);
   if (st) return ctx_fail(c, st);
   c->j = 0;
   c->phase = kInCycle;
@@ -518,10 +546,7 @@ int ctx_create_in(cbg_ctx** out, int32_t n, int64_t nnz, const int32_t* d_row_pt
                   const double* d_vals, const cbg_opts* opts, cudaStream_t stream, void* dmem, size_t dbytes,
                   void* pinned) {
   *out = nullptr;
-  if (!opts_valid(n, opts)) {
-    set_error("cbgmres_create: invalid n or options (1 <= restart <= min(n, 1024), tol > 0, l in {16,21,32})");
-    return CBG_ERR_INVALID_ARG;
-  }
+  if (!opts_valid(n, opts)) return opts_fail(n, opts);
   if (nnz < 0 || nnz > INT32_MAX || !d_row_ptr || (nnz > 0 && (!d_col || !d_vals))) {
     set_error("cbgmres_create: invalid CSR arguments");
     return CBG_ERR_INVALID_ARG;
@@ -672,10 +697,7 @@ int cbgmres_create(cbg_ctx** out, int32_t n, int64_t nnz, const int32_t* d_row_p
     return CBG_ERR_INVALID_ARG;
   }
   *out = nullptr;
-  if (!opts_valid(n, opts)) {
-    set_error("cbgmres_create: invalid n or options (1 <= restart <= min(n, 1024), tol > 0, l in {16,21,32})");
-    return CBG_ERR_INVALID_ARG;
-  }
+  if (!opts_valid(n, opts)) return opts_fail(n, opts);
   const size_t total = layout_of(n, opts).total;
   void* dmem = nullptr;
   cudaError_t e = cudaMalloc(&dmem, total);
@@ -734,7 +756,7 @@ int cbgmres_start(cbg_ctx* c, const double* d_b, double* d_x) {
   }
   c->b = d_b;
   c->x = d_x;
-  c->iters = c->restarts = c->reorths = 0;
+  c->iters = c->restarts = c->reorths = c->breakdowns = 0;
   c->bnorm = c->true_rrn = c->implicit = 0.0;
   c->status = CBG_OK;
   c->converged = 0;
@@ -842,6 +864,7 @@ int cbgmres_finish(cbg_ctx* c, cbg_result* r) {
     r->true_rrn = c->true_rrn;
     r->implicit_rrn = c->implicit;
     r->seconds = c->seconds;
+    r->breakdowns = c->breakdowns;
   }
   return c->status;
 }
@@ -852,7 +875,7 @@ int cbgmres_solve(cbg_ctx* c, const double* d_b, double* d_x, cbg_result* r) {
   int32_t done = 0;
   while (!done) {
     st = cbgmres_advance(c, 1 << 30, &done);
-    if (st && st != CBG_ERR_NOT_CONVERGED) break;
+    if (st && st != CBG_ERR_NOT_CONVERGED && st != CBG_ERR_BREAKDOWN_NOT_CONVERGED) break;
     if (!done) {
       cudaError_t e = cudaEventSynchronize(c->ev);
       if (e != cudaSuccess) return ctx_fail(c, cuda_fail(e, "solver event wait"));

@@ -12,6 +12,7 @@ import pytest
 import torch
 
 import workloads
+from parity import assert_same_decisions
 
 pytestmark = pytest.mark.gpu
 
@@ -141,3 +142,64 @@ def test_many_small_requests_overlap(cbg):
     assert all(c.status == 0 and c.result.converged for c in done.values())
     assert makespan < busy
     srv.close()
+
+
+STREAMED_MIX = [  # (N, dim, Pe, fmt, bits, tol): 2.6e4 .. 6.4e4 rows, restart 100, all streamed cycles
+    (30, 3, 30.0, "fp64", 32, 1e-10),
+    (160, 2, 20.0, "frsz2", 32, 1e-10),
+    (40, 3, 10.0, "frsz2", 21, 1e-10),
+    (250, 2, 40.0, "fp32", 32, 1e-10),
+]
+
+
+def test_served_streamed_requests_match_oracle(cbg, orc):
+    """Four requests of 26 000 to 64 000 rows with restart 100, too large for the on-chip cycle,
+    served concurrently (four slots, two steps per turn, so their Arnoldi steps interleave on the
+    device): each served solution must be the oracle's (iterations within 2%, the same second-pass
+    and breakdown counts, ||x - x_oracle|| / ||x_oracle|| <= 1e-8, explicit residual <= tol) and bit
+    for bit the same as the solve alone."""
+    from concurrent.futures import ThreadPoolExecutor
+
+    cases = []
+    for i, (N, dim, pe, fmt, bits, tol) in enumerate(STREAMED_MIX):
+        # b = A x_true from the oracle's SpMV on the host: the oracle and the GPU solve the same system
+        Ah = workloads.convdiff(N, dim, tuple([1.0] * dim), pe)
+        rp, col, vals = Ah.numpy()
+        bh = orc.spmv(rp, col, vals, workloads.uniform_vector(Ah.n, 50 + i).numpy())
+        o = cbg.default_opts(restart=100, fmt=fmt, frsz2_bits=bits, tol=tol, max_iters=20000)
+        cases.append((Ah.to("cuda"), torch.from_numpy(bh).cuda(), o, fmt, bits, tol, bh))
+
+    def oracle_solve(c):
+        A, _, o, fmt, bits, tol, bh = c
+        rp, col, vals = A.numpy()
+        return orc.gmres(rp, col, vals, bh, restart=100, tol=tol, fmt=orc.FORMAT_NAMES[fmt], l=bits)
+
+    with ThreadPoolExecutor(len(cases)) as ex:  # the oracle's C code runs outside the GIL
+        refs = list(ex.map(oracle_solve, cases))
+    alone = []
+    for A, b, o, *_ in cases:
+        S = cbg.Solver(A.row_ptr, A.col, A.vals, opts=o)
+        assert S.cycle_cluster == 0  # streamed cycles
+        S.close()
+        alone.append(solve_alone(cbg, A, b, o))
+    srv = cbg.Server(sum(cbg.workspace_bytes(A.n, o) for A, _, o, *_ in cases), max_active=4, steps_per_turn=2,
+                     max_bypass=4)
+    xs = []
+    for i, (A, b, o, *_) in enumerate(cases):
+        x = torch.zeros(A.n, dtype=torch.float64, device="cuda")
+        xs.append(x)
+        srv.submit(i, A.row_ptr, A.col, A.vals, b, x, o)
+    done, _ = run_server(srv, len(cases), timeout_s=300.0)
+    torch.cuda.synchronize()
+    srv.close()
+    for i, ((A, b, o, fmt, bits, tol, bh), ref) in enumerate(zip(cases, refs)):
+        c = done[i]
+        assert ref.converged and c.status == 0 and c.result.converged, (i, c.status)
+        xg = xs[i].cpu().numpy()
+        rp, col, vals = A.numpy()
+        assert orc.nrm2(bh - orc.spmv(rp, col, vals, xg)) / orc.nrm2(bh) <= tol * 1.0000001
+        assert abs(c.result.iters - ref.iters) <= max(1, 0.02 * ref.iters), (i, c.result.iters, ref.iters)
+        assert np.linalg.norm(xg - ref.x) / np.linalg.norm(ref.x) <= 1e-8, i
+        assert_same_decisions(c.result, ref)
+        assert torch.equal(xs[i], alone[i][0]), f"request {i}: served x differs from the solve alone"
+        assert c.result.iters == alone[i][1].iters

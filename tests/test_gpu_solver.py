@@ -10,6 +10,7 @@ import pytest
 import torch
 
 import workloads
+from parity import assert_same_decisions
 
 pytestmark = pytest.mark.gpu
 
@@ -109,11 +110,15 @@ def test_gmres_c1_parity(cbg, orc, c1_inverse_norm, fmt, l, cycle):
             idx = np.random.default_rng(s).integers(0, A.n, 8)
             bb[idx] = np.nextafter(bb[idx], np.inf)
             band.append(orc.gmres(rp, col, vals, bb, restart=50, tol=1e-10, fmt=orc.FORMAT_NAMES[fmt], l=l).iters)
-        assert 0.98 * min(band) <= r.iters <= 1.02 * max(band), (r.iters, min(band), max(band))
+        # measured band on this system: fp16 257-283 (10% wide), bf16 365-417 (14% wide)
+        assert 0.98 * min(band) <= r.iters <= 1.02 * max(band), \
+            (f"{fmt}: GPU {r.iters} steps outside the oracle's band {min(band)}-{max(band)} "
+             f"({(max(band) - min(band)) / min(band):.0%} wide) +-2%")
         assert np.linalg.norm(xg - ref.x) <= 1.01 * c1_inverse_norm * (res_g + res_o)
     else:
         assert abs(r.iters - ref.iters) <= max(1, 0.02 * ref.iters), (r.iters, ref.iters)
         assert dx <= 1e-8, dx
+        assert_same_decisions(r, ref)
 
 
 def test_gmres_3d_parity_and_history(cbg, orc):
@@ -128,6 +133,7 @@ def test_gmres_3d_parity_and_history(cbg, orc):
     assert r.converged
     assert abs(r.iters - ref.iters) <= max(1, 0.02 * ref.iters)
     assert np.linalg.norm(x.cpu().numpy() - ref.x) / np.linalg.norm(ref.x) <= 1e-8
+    assert_same_decisions(r, ref)
     hist = S.history()
     assert hist.size == r.iters
     # implicit residual history matches the oracle's where both ran the same steps
@@ -184,6 +190,7 @@ def test_gmres_powerlaw_parity(cbg, orc):
     assert abs(r.iters - ref.iters) <= max(1, 0.02 * ref.iters)
     xo = ref.x
     assert np.linalg.norm(x.cpu().numpy() - xo) / np.linalg.norm(xo) <= 1e-8
+    assert_same_decisions(r, ref)
 
 
 @pytest.mark.parametrize("fmt,l,bound", [("fp64", 32, 1e-12), ("frsz2", 32, 1e-7)])
@@ -227,6 +234,7 @@ def test_gmres_jacobi_parity(cbg, orc, fmt, l):
     assert ref.converged and r.converged and r.true_rrn <= 1e-10
     assert abs(r.iters - ref.iters) <= max(1, 0.02 * ref.iters)
     assert np.linalg.norm(x.cpu().numpy() - ref.x) / np.linalg.norm(ref.x) <= 1e-8
+    assert_same_decisions(r, ref)
     r0 = orc.gmres(rp, col, vals, b, restart=30, tol=1e-10, fmt=orc.FORMAT_NAMES[fmt], l=l)
     assert ref.iters < r0.iters
 
@@ -313,6 +321,7 @@ def test_onchip_restart_100_parity(cbg, orc, fmt, l):
     assert r.converged and r.true_rrn <= 1e-10
     assert abs(r.iters - ref.iters) <= max(1, 0.02 * ref.iters), (r.iters, ref.iters)
     assert np.linalg.norm(x.cpu().numpy() - ref.x) / np.linalg.norm(ref.x) <= 1e-8
+    assert_same_decisions(r, ref)
 
 
 @pytest.mark.parametrize("cycle", ["auto", "streamed"])
@@ -336,3 +345,110 @@ def test_tiny_systems(cbg, orc, cycle, N, dim):
     assert r.converged and r.true_rrn <= 1e-12
     assert abs(r.iters - ref.iters) <= 2, (r.iters, ref.iters)
     assert np.linalg.norm(x.cpu().numpy() - ref.x) / np.linalg.norm(ref.x) <= 1e-10
+
+
+# ---- the second Gram-Schmidt pass (Fig. 1 steps 7-11) and the breakdown exit (step 12) -----------
+# The hand-derived cases of tests/test_oracle_gmres.py: their counts are fixed by Fig. 1, and the
+# oracle is pinned to them; the GPU must take the same decisions on both ways of running a cycle.
+
+def _small_csr(rows):
+    rp, col, vals = [0], [], []
+    for r in rows:
+        for c, v in r:
+            col.append(c)
+            vals.append(v)
+        rp.append(len(col))
+    return (torch.tensor(rp, dtype=torch.int32, device="cuda"), torch.tensor(col, dtype=torch.int32, device="cuda"),
+            torch.tensor(vals, dtype=torch.float64, device="cuda"))
+
+
+@pytest.mark.parametrize("cycle", ["auto", "streamed"])
+@pytest.mark.parametrize("fmt,l", [("fp64", 32), ("frsz2", 32), ("frsz2", 16), ("fp32", 32)])
+def test_second_pass_and_breakdown_hand_derived(cbg, orc, cycle, fmt, l):
+    """A = diag(1, 1, 1/8, 1/8), b = 1: step 1 takes the second pass (||w|| = 0.614 omega), step 2
+    finds w = 0 exactly (second pass and breakdown): 2 iterations, 2 second passes, 1 breakdown.
+    The GPU's normalisation v_2 = w / h must be the correctly rounded quotient (here exactly
+    (1, 1, -1, -1)/2) for step 2 to find w = 0."""
+    rp, col, vals = _small_csr([[(0, 1.0)], [(1, 1.0)], [(2, 0.125)], [(3, 0.125)]])
+    ref = orc.gmres(rp.cpu().numpy(), col.cpu().numpy(), vals.cpu().numpy(), np.ones(4), restart=4, tol=1e-14,
+                    fmt=orc.FORMAT_NAMES[fmt], l=l)
+    assert (ref.iters, ref.reorths, ref.breakdowns) == (2, 2, 1)
+    S = cbg.Solver(rp, col, vals, restart=4, tol=1e-14, fmt=fmt, frsz2_bits=l, cycle=cycle)
+    x = torch.zeros(4, dtype=torch.float64, device="cuda")
+    r = S.solve(torch.ones(4, dtype=torch.float64, device="cuda"), x)
+    S.close()
+    assert r.status == 0 and r.converged
+    assert (r.iters, r.reorths, r.breakdowns, r.restarts) == (2, 2, 1, 1)
+    assert np.allclose(x.cpu().numpy(), [1.0, 1.0, 8.0, 8.0], rtol=1e-14, atol=0)
+
+
+@pytest.mark.parametrize("cycle", ["auto", "streamed"])
+def test_no_second_pass_when_av_is_orthogonal_to_v(cbg, cycle):
+    """A = [[0, 1], [-1, 0]], b = (1, 0), restart 1: A v is orthogonal to v at every step, so no
+    step takes the second pass; x stays 0 and the solve ends at max_iters (5)."""
+    rp, col, vals = _small_csr([[(1, 1.0)], [(0, -1.0)]])
+    S = cbg.Solver(rp, col, vals, restart=1, tol=1e-12, fmt="fp64", max_iters=5, cycle=cycle)
+    x = torch.zeros(2, dtype=torch.float64, device="cuda")
+    r = S.solve(torch.tensor([1.0, 0.0], dtype=torch.float64, device="cuda"), x)
+    S.close()
+    assert r.status == -5 and not r.converged
+    assert (r.iters, r.reorths, r.breakdowns, r.restarts) == (5, 0, 0, 5)
+    assert float(x.abs().max()) == 0.0 and r.true_rrn == 1.0
+
+
+@pytest.mark.parametrize("cycle", ["auto", "streamed"])
+def test_breakdown_without_progress_is_reported(cbg, cycle):
+    """A = [[0, 1], [0, 0]], b = (0, 1) has no solution: step 2 breaks down (h = 0) and the
+    restart's residual is unchanged, so the solve stops with CBG_ERR_BREAKDOWN_NOT_CONVERGED after
+    2 iterations and 1 cycle, as the oracle does (its reading R18), rather than running to max_iters."""
+    rp, col, vals = _small_csr([[(1, 1.0)], []])
+    S = cbg.Solver(rp, col, vals, restart=2, tol=1e-12, fmt="fp64", max_iters=100, cycle=cycle)
+    x = torch.zeros(2, dtype=torch.float64, device="cuda")
+    r = S.solve(torch.tensor([0.0, 1.0], dtype=torch.float64, device="cuda"), x)
+    S.close()
+    assert r.status == -9 and not r.converged
+    assert (r.iters, r.reorths, r.breakdowns, r.restarts) == (2, 0, 1, 1)
+    assert float(x.abs().max()) == 0.0 and r.true_rrn == 1.0
+
+
+def _shifted_32x32():
+    """The C1 operator on a 32x32 grid with 6 added to its diagonal: well conditioned, so even an
+    11- or 8-bit basis converges in a step count that one-ulp changes of b do not move (the
+    oracle: fp16 32 steps, bf16 41, the same for 24 perturbed right-hand sides)."""
+    A = workloads.convdiff(32, 2, (1.0, 0.5), 10.0)
+    rp, col, vals = A.numpy()
+    vals = vals.copy()
+    rows = np.repeat(np.arange(A.n), np.diff(rp))
+    vals[col == rows] += 6.0
+    return rp, col, vals
+
+
+@pytest.mark.parametrize("cycle", ["auto", "streamed"])
+@pytest.mark.parametrize("fmt", ["fp16", "bf16"])
+def test_gmres_fp16_bf16_strict_bar(cbg, orc, fmt, cycle):
+    """fp16 and bf16 bases at the benchmark spec's own bar, on systems where their step counts are not
+    chaotic: the shifted 32x32 operator (restart 50) and the power-law matrix with the Jacobi
+    preconditioner (restart 30): tolerance reached, steps within 2% of the oracle's,
+    ||x - x_oracle|| / ||x_oracle|| <= 1e-8, the same second-pass and breakdown decisions."""
+    cases = []
+    rp, col, vals = _shifted_32x32()
+    cases.append((rp, col, vals, workloads.uniform_vector(rp.size - 1, 0).numpy(), 50, "none"))
+    P = workloads.powerlaw(3000, seed=3)
+    prp, pcol, pvals = P.numpy()
+    cases.append((prp, pcol, pvals, np.ones(P.n), 30, "jacobi"))
+    for rp, col, vals, xt, restart, precond in cases:
+        if precond == "jacobi" and cycle == "auto":
+            continue  # long rows: the power-law matrix always takes the streamed cycle
+        b = orc.spmv(rp, col, vals, xt)
+        ref = orc.gmres(rp, col, vals, b, restart=restart, tol=1e-10, fmt=orc.FORMAT_NAMES[fmt], precond=precond)
+        assert ref.converged
+        S = cbg.Solver(torch.from_numpy(rp).cuda(), torch.from_numpy(col).cuda(), torch.from_numpy(vals).cuda(),
+                       restart=restart, tol=1e-10, fmt=fmt, precond=precond, cycle=cycle)
+        x = torch.zeros(rp.size - 1, dtype=torch.float64, device="cuda")
+        r = S.solve(torch.from_numpy(b).cuda(), x)
+        S.close()
+        xg = x.cpu().numpy()
+        assert r.status == 0 and r.converged and r.true_rrn <= 1e-10
+        assert abs(r.iters - ref.iters) <= max(1, 0.02 * ref.iters), (precond, r.iters, ref.iters)
+        assert np.linalg.norm(xg - ref.x) / np.linalg.norm(ref.x) <= 1e-8
+        assert_same_decisions(r, ref)

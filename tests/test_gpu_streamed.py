@@ -1,0 +1,102 @@
+"""Solve parity at the streamed cycle's full-grid kernel shapes, against the oracle.
+
+The 3D convection-diffusion operator of the 256^3 benchmark system (7-point stencil, wind (1,1,1),
+Peclet 50) on a 48^3 grid (n = 110 592), b = A 1, x0 = 0, restart 100 (the Methodology's restart
+length), tol 1e-10, solved with cycle="streamed" in the fp64 and the three FRSZ2 bases. At this size
+the basis update runs its two-stage full-grid instance (the grid needs more CTAs than the GPU has
+SMs) and the dot spans the GPU, as at the benchmark's sizes; the smaller solve tests run the on-chip
+cycle or the deep-pipeline instance instead.
+
+Bar (the benchmark spec's): the explicit relative residual reaches the tolerance, the Arnoldi step count
+is within 2% of the oracle's (for FRSZ2-16 and FRSZ2-21, whose counts move by 2-3% on the oracle
+itself when b moves by one ulp, within 2% of that band), ||x - x_oracle|| / ||x_oracle|| <= 1e-8,
+and the second Gram-Schmidt
+pass (Fig. 1 steps 7-11) and the breakdown exit (step 12) are taken as often as the oracle takes
+them. The oracle's solves of this system are also committed as tests/golden/solve_c3m_<format>.json
+(tests/golden/make_solve_references.py); the live oracle must reproduce them."""
+import json
+import os
+from concurrent.futures import ThreadPoolExecutor
+
+import numpy as np
+import pytest
+import torch
+
+import workloads
+from parity import assert_same_decisions
+
+pytestmark = [pytest.mark.gpu, pytest.mark.slow]
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+FORMATS = [("fp64", 32), ("frsz2", 16), ("frsz2", 21), ("frsz2", 32)]
+
+
+def fname(fmt, l):
+    return fmt if fmt != "frsz2" else f"frsz2_{l}"
+
+
+@pytest.fixture(scope="module")
+def mid(orc):
+    A = workloads.convdiff(48, 3, (1.0, 1.0, 1.0), 50.0)
+    rp, col, vals = A.numpy()
+    b = orc.spmv(rp, col, vals, np.ones(A.n))
+
+    def solve(f):  # ctypes releases the GIL: the four oracle solves run side by side
+        return orc.gmres(rp, col, vals, b, restart=100, tol=1e-10, fmt=orc.FORMAT_NAMES[f[0]], l=f[1])
+
+    with ThreadPoolExecutor(len(FORMATS)) as ex:
+        refs = dict(zip(FORMATS, ex.map(solve, FORMATS)))
+    return A, b, refs
+
+
+def step_band(fmt, l, ref_iters):
+    """The oracle's step counts on this system: its own, and the spread over right-hand sides one ulp
+    away (stored with the committed record). FRSZ2-32 and fp64 do not move (398 for every one of
+    them); the 21- and 16-bit bases do (the oracle: FRSZ2-21 414-425, FRSZ2-16 425-434, 2-3% wide),
+    so for those the 2% bar is taken around that band, as for fp16 and bf16 on C1."""
+    with open(os.path.join(ROOT, "tests", "golden", f"solve_c3m_{fname(fmt, l)}.json")) as f:
+        rec = json.load(f)
+    band = [ref_iters] + rec.get("iters_perturbed_b", [])
+    return min(band), max(band)
+
+
+@pytest.mark.parametrize("fmt,l", FORMATS)
+def test_streamed_mid_size_parity(cbg, orc, mid, fmt, l):
+    A, b, refs = mid
+    ref = refs[(fmt, l)]
+    assert ref.converged
+    Ad = A.to("cuda")
+    S = cbg.Solver(Ad.row_ptr, Ad.col, Ad.vals, restart=100, tol=1e-10, fmt=fmt, frsz2_bits=l, cycle="streamed")
+    assert S.cycle_cluster == 0
+    x = torch.zeros(A.n, dtype=torch.float64, device="cuda")
+    r = S.solve(torch.from_numpy(b).cuda(), x)
+    S.close()
+    xg = x.cpu().numpy()
+    assert r.status == 0 and r.converged and r.true_rrn <= 1e-10
+    rp, col, vals = A.numpy()
+    assert orc.nrm2(b - orc.spmv(rp, col, vals, xg)) / orc.nrm2(b) <= 1.0000001e-10
+    lo, hi = step_band(fmt, l, ref.iters)
+    assert 0.98 * lo <= r.iters <= 1.02 * hi, (f"{fmt}{l}: GPU {r.iters} steps, oracle {ref.iters}, oracle band "
+                                               f"{lo}-{hi} ({(hi - lo) / lo:.1%} wide) +-2%")
+    if lo == hi:
+        assert abs(r.iters - ref.iters) <= max(1, 0.02 * ref.iters), (r.iters, ref.iters)
+    assert np.linalg.norm(xg - ref.x) / np.linalg.norm(ref.x) <= 1e-8
+    assert_same_decisions(r, ref)
+
+
+@pytest.mark.parametrize("fmt,l", FORMATS)
+def test_committed_mid_size_reference_reproduces(mid, fmt, l):
+    """The committed record of the oracle's solve is what the oracle computes on this host, bit for
+    bit: the oracle uses IEEE operations only (its Givens length is sqrt(a*a + b*b), not a library
+    hypot, whose rounding differs between C libraries), so its results do not depend on the host."""
+    import hashlib
+
+    A, b, refs = mid
+    ref = refs[(fmt, l)]
+    path = os.path.join(ROOT, "tests", "golden", f"solve_c3m_{fname(fmt, l)}.json")
+    with open(path) as f:
+        rec = json.load(f)
+    assert (rec["iters"], rec["reorths"], rec["breakdowns"], rec["restarts"]) == \
+        (ref.iters, ref.reorths, ref.breakdowns, ref.restarts)
+    assert rec["true_rrn"] == ref.true_rrn
+    assert rec["x_sha256"] == hashlib.sha256(np.ascontiguousarray(ref.x).tobytes()).hexdigest()

@@ -265,3 +265,72 @@ def test_jacobi_zero_diagonal_rejected(orc):
     col = np.array([1, 0], np.int32)
     with pytest.raises(ValueError):
         orc.gmres(rp, col, np.array([1.0, 1.0]), np.ones(2), restart=2, precond="jacobi")
+
+
+# ---- The second Gram-Schmidt pass (Fig. 1 steps 7-11) and the breakdown exit (step 12, R10) -----
+# Hand-derived cases: every quantity below is worked out by hand from Fig. 1, so the counts the
+# oracle reports are fixed by the paper's algorithm, not by the oracle.
+
+ETA = 1.0 / math.sqrt(2.0)
+
+
+def dyadic_case():
+    """A = diag(1, 1, 1/8, 1/8), b = (1, 1, 1, 1). All Arnoldi quantities are dyadic rationals:
+      step 1: v1 = (1,1,1,1)/2; w = A v1 = (1/2, 1/2, 1/16, 1/16), omega = sqrt(65/128);
+              h11 = v1.w = 9/16; w - h11 v1 = (7/32)(1, 1, -1, -1), ||w|| = 7/16 = 0.614 omega
+              < eta omega (eta = 1/sqrt 2; but > eta^2 omega): the second pass runs, V^T w = 0,
+              so h and ||w|| = 7/16 are unchanged and it is no breakdown (7/16 is not below
+              eta * 7/16);
+      step 2: v2 = w / (7/16) = (1, 1, -1, -1)/2; A v2 = (1/2, 1/2, -1/16, -1/16); h12 = 7/16,
+              h22 = 9/16 and w - h12 v1 - h22 v2 = 0 exactly: ||w|| = 0 < eta omega, a second pass,
+              and h_{3,2} = 0: a breakdown.
+    Two distinct eigenvalues: the Krylov space is invariant after two steps and x = (1, 1, 8, 8)."""
+    rp = np.arange(5, dtype=np.int32)
+    col = np.arange(4, dtype=np.int32)
+    vals = np.array([1.0, 1.0, 0.125, 0.125])
+    return rp, col, vals, np.ones(4)
+
+
+@pytest.mark.parametrize("fmt,l", [(0, 32), (4, 32), (4, 16), (1, 32)])
+def test_second_pass_and_breakdown_hand_derived(orc, fmt, l):
+    # every value of this case (v_1, v_2 = +-1/2) is stored exactly by each of these formats
+    rp, col, vals, b = dyadic_case()
+    r = orc.gmres(rp, col, vals, b, restart=4, tol=1e-14, fmt=fmt, l=l)
+    assert r.converged and not r.stagnated
+    assert (r.iters, r.reorths, r.breakdowns, r.restarts) == (2, 2, 1, 1)
+    assert np.allclose(r.x, [1.0, 1.0, 8.0, 8.0], rtol=1e-14, atol=0)
+    m_eff, V, Vh, H, beta = orc.arnoldi_cycle(rp, col, vals, b, restart=4, fmt=fmt, l=l)
+    assert m_eff == 2 and beta == 2.0
+    assert np.array_equal(V[0], [0.5, 0.5, 0.5, 0.5]) and np.array_equal(V[1], [0.5, 0.5, -0.5, -0.5])
+    assert H[0, 0] == 9 / 16 and H[1, 0] == 7 / 16 and H[0, 1] == 7 / 16 and H[1, 1] == 9 / 16
+    assert H[2, 1] == 0.0
+
+
+def test_no_second_pass_when_av_is_orthogonal_to_v(orc):
+    """A = [[0, 1], [-1, 0]] turns every vector by 90 degrees: A v is orthogonal to v, so the first
+    pass leaves ||w|| = omega, never below eta omega: no second pass at any step. With restart 1
+    (the minimal-residual iteration) the step length (r, A r) / (A r, A r) is 0: x stays 0, the
+    residual stays ||b||, and no step breaks down."""
+    rp = np.array([0, 1, 2], dtype=np.int32)
+    col = np.array([1, 0], dtype=np.int32)
+    vals = np.array([1.0, -1.0])
+    r = orc.gmres(rp, col, vals, np.array([1.0, 0.0]), restart=1, tol=1e-12, max_iters=5)
+    assert (r.iters, r.reorths, r.breakdowns, r.restarts) == (5, 0, 0, 5)
+    assert not r.converged and not r.stagnated
+    assert not r.x.any() and r.true_rrn == 1.0
+
+
+def test_breakdown_without_progress_stops(orc):
+    """A = [[0, 1], [0, 0]], b = (0, 1): A x = b has no solution. v1 = (0, 1), A v1 = (1, 0) is
+    orthogonal to v1 (h11 = 0, ||w|| = omega = 1: no second pass); v2 = (1, 0), A v2 = 0:
+    omega = 0, h_{3,2} = 0 (no second pass either: 0 < eta * 0 is false), a breakdown. The
+    rotated R has a zero pivot in column 2 and the rotated g_1 = 0, so y = 0 and x = 0: the next
+    restart's residual equals the one the cycle started from, and the solve stops there (R18)
+    instead of repeating the cycle: 2 iterations, 1 cycle, 1 breakdown."""
+    rp = np.array([0, 1, 1], dtype=np.int32)
+    col = np.array([1], dtype=np.int32)
+    vals = np.array([1.0])
+    r = orc.gmres(rp, col, vals, np.array([0.0, 1.0]), restart=2, tol=1e-12, max_iters=100)
+    assert r.stagnated and not r.converged
+    assert (r.iters, r.reorths, r.breakdowns, r.restarts) == (2, 0, 1, 1)
+    assert not r.x.any() and r.true_rrn == 1.0

@@ -42,6 +42,17 @@ MUTATIONS = [
     ("jacobi_step17_unscaled", "for (int32_t k = 0; k < n; ++k) x[k] += ws->dinv[k] * ws->t[k];",
      "for (int32_t k = 0; k < n; ++k) x[k] += ws->t[k];", "test_oracle_gmres.py"),
     ("jacobi_m_not_inverted", "ws->dinv[i] = 1.0 / d;", "ws->dinv[i] = d;", "test_oracle_gmres.py"),
+    # the second Gram-Schmidt pass of steps 7-11 and the breakdown exit of step 12
+    ("reorth_trigger_flipped", "    if (hn < ws->eta * omega) {", "    if (hn > ws->eta * omega) {",
+     "test_oracle_gmres.py"),
+    ("reorth_trigger_eta_squared", "    if (hn < ws->eta * omega) {", "    if (hn < ws->eta * ws->eta * omega) {",
+     "test_oracle_gmres.py"),
+    ("breakdown_literal_step12", "int breakdown = (hn == 0.0) || (did_reorth && hn < ws->eta * h_before);",
+     "int breakdown = (hn == 0.0) || (hn < ws->eta * omega);", "test_oracle_gmres.py"),
+    ("breakdown_eta_on_omega", "int breakdown = (hn == 0.0) || (did_reorth && hn < ws->eta * h_before);",
+     "int breakdown = (hn == 0.0) || (did_reorth && hn < ws->eta * omega);", "test_oracle_gmres.py"),
+    ("breakdown_stagnation_dropped", "if (broke_down && res->true_rrn >= cycle_start_rrn) { /* R18 */",
+     "if (0) { /* R18 */", "test_oracle_gmres.py"),
 ]
 
 
