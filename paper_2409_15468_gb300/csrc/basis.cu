@@ -297,7 +297,8 @@ int basis_launch_config(const void* fn, int threads, size_t smem, int64_t units,
 namespace {
 
 int cast_dot_launch(const BasisView& B, int nvec, const double* w, double* out, double* partials,
-                    unsigned int* counter, const Gate& gate, int max_grid, cudaStream_t stream) {
+                    unsigned int* counter, int* err, const Gate& gate, int max_grid, cudaStream_t stream) {
+  if (B.fmt == CBG_FP16) return fp16_dot_launch(B, nvec, w, out, partials, counter, err, gate, max_grid, stream);
   const void* fn;
   switch (B.fmt) {
     case CBG_FP64: fn = fnp(k_dot_cast<CBG_FP64>); break;
@@ -338,7 +339,7 @@ int launch_basis_dot(const BasisView& B, int nvec, const double* w, double* out,
                      int* err, const Gate& gate, cudaStream_t stream) {
   if (nvec <= 0 || B.n <= 0) return CBG_OK;
   if (B.fmt == CBG_FRSZ2) return frsz2_dot_launch(B, nvec, w, out, partials, counter, err, gate, kMaxGrid, stream);
-  return cast_dot_launch(B, nvec, w, out, partials, counter, gate, kMaxGrid, stream);
+  return cast_dot_launch(B, nvec, w, out, partials, counter, err, gate, kMaxGrid, stream);
 }
 
 // The basis dot with the grid limited to max_grid CTAs, for callers whose partial-sum buffer has a
@@ -348,7 +349,7 @@ int launch_basis_dot_capped(const BasisView& B, int nvec, const double* w, doubl
   if (nvec <= 0 || B.n <= 0) return CBG_OK;
   const Gate gate{nullptr, nullptr};
   if (B.fmt == CBG_FRSZ2) return frsz2_dot_launch(B, nvec, w, out, partials, counter, err, gate, max_grid, stream);
-  return cast_dot_launch(B, nvec, w, out, partials, counter, gate, max_grid, stream);
+  return cast_dot_launch(B, nvec, w, out, partials, counter, err, gate, max_grid, stream);
 }
 
 int launch_basis_update(const BasisView& B, int nvec, const int* nvec_dev, const double* h, int negate, double* w,
@@ -357,6 +358,8 @@ int launch_basis_update(const BasisView& B, int nvec, const int* nvec_dev, const
   if ((nvec <= 0 && !nvec_dev) || B.n <= 0) return CBG_OK;
   if (B.fmt == CBG_FRSZ2)
     return frsz2_update_launch(B, nvec, nvec_dev, h, negate, w, partials, counter, err, epi, gate, stream);
+  if (B.fmt == CBG_FP16)
+    return fp16_update_launch(B, nvec, nvec_dev, h, negate, w, partials, counter, err, epi, gate, stream);
   const void* fn;
   switch (B.fmt) {
     case CBG_FP64: fn = fnp(k_update_cast<CBG_FP64>); break;

@@ -22,6 +22,7 @@
 // warp); thread 0 refills the stage released one iteration earlier, so warps never wait on each
 // other inside the vector loop. Every wait is bounded (globaltimer); on expiry the kernel records
 // kDevErrTimeout, waits (bounded) for its own copies in flight and returns.
+#include "decode.cuh"
 #include "frsz2_block.cuh"
 
 namespace cbg {
@@ -33,18 +34,52 @@ namespace cbg {
 // blocks alone leave the GPU underfilled)
 // ================================================================================================
 
-template <int L>
+// Pipeline shape of the dot per code width (threads = blocks per tile, vectors per stage, stages);
+// the defaults are the measured best, and each can be set at build time (-DCBG_DOT_<knob>_<l>=...)
+// for a sweep.
+#ifndef CBG_DOT_THREADS_16
+#define CBG_DOT_THREADS_16 256
+#endif
+#ifndef CBG_DOT_THREADS_21
+#define CBG_DOT_THREADS_21 128
+#endif
+#ifndef CBG_DOT_THREADS_32
+#define CBG_DOT_THREADS_32 128
+#endif
+#ifndef CBG_DOT_VPS_16
+#define CBG_DOT_VPS_16 2
+#endif
+#ifndef CBG_DOT_VPS_21
+#define CBG_DOT_VPS_21 2
+#endif
+#ifndef CBG_DOT_VPS_32
+#define CBG_DOT_VPS_32 2
+#endif
+#ifndef CBG_DOT_STAGES_16
+#define CBG_DOT_STAGES_16 2
+#endif
+#ifndef CBG_DOT_STAGES_21
+#define CBG_DOT_STAGES_21 2
+#endif
+#ifndef CBG_DOT_STAGES_32
+#define CBG_DOT_STAGES_32 2
+#endif
+
+// FDot<16, true> is the same pipeline over a basis stored as binary16 (64 bytes per 32-value block,
+// as an l = 16 block, and no exponent words): every value below 2 in magnitude is an exact integer
+// in units of 2^-24 (fp16_fixed), so a block's dot is the same exact integer sum.
+template <int L, bool H = false>
 struct FDot {
   // 128 threads (blocks) per tile; 256 at l = 16, whose 8 KB per-vector copies then grow to 16 KB
   // (3.7% faster there)
-  static constexpr int kThreads = L == 16 ? 256 : 128;
+  static constexpr int kThreads = L == 16 ? CBG_DOT_THREADS_16 : (L == 21 ? CBG_DOT_THREADS_21 : CBG_DOT_THREADS_32);
   static constexpr int kWarps = kThreads / 32;
-  static constexpr int kVps = 2;        // basis vectors per pipeline stage
-  static constexpr int kStages = 2;
+  static constexpr int kVps = L == 16 ? CBG_DOT_VPS_16 : (L == 21 ? CBG_DOT_VPS_21 : CBG_DOT_VPS_32);
+  static constexpr int kStages = L == 16 ? CBG_DOT_STAGES_16 : (L == 21 ? CBG_DOT_STAGES_21 : CBG_DOT_STAGES_32);
   static constexpr int kBatch = 4;       // vectors per per-warp reduction
   static constexpr int kRedStride = 33;  // doubles per batch row (padded against bank conflicts)
   static constexpr int kCodeBytes = kThreads * L * 4;
-  static constexpr int kVecBytes = kCodeBytes + kThreads * 4;  // one vector's codes and exponents
+  static constexpr int kVecBytes = kCodeBytes + (H ? 0 : kThreads * 4);  // one vector's codes and exponents
   static constexpr int kStageBytes = kVps * kVecBytes;
   static constexpr int kRedDoubles = kWarps * kBatch * kRedStride;
   static size_t smem_bytes(int nvec) {
@@ -53,12 +88,12 @@ struct FDot {
   }
 };
 
-template <int L>
-__global__ void __launch_bounds__(FDot<L>::kThreads) k_dot_frsz2(BasisView B, int nvec, const double* __restrict__ w,
-                                                                 double* __restrict__ out,
-                                                                 double* __restrict__ partials,
-                                                                 unsigned int* counter, int* err, Gate gate) {
-  using C = FDot<L>;
+template <int L, bool H>
+__device__ __forceinline__ void dot_body(const BasisView& B, int nvec, const double* __restrict__ w,
+                                         double* __restrict__ out, double* __restrict__ partials,
+                                         unsigned int* counter, int* err, const Gate& gate) {
+  static_assert(!H || L == 16, "binary16 blocks have the l = 16 layout");
+  using C = FDot<L, H>;
   constexpr int T = C::kThreads, S = C::kStages;
   if (gate_skip(gate)) return;
   extern __shared__ __align__(128) uint8_t smem[];
@@ -99,15 +134,16 @@ __global__ void __launch_bounds__(FDot<L>::kThreads) k_dot_frsz2(BasisView B, in
     const int64_t tb0 = b0 + (int64_t)tile * T;
     const int nbt = static_cast<int>(min((int64_t)T, b1 - tb0));
     const uint32_t cbytes = static_cast<uint32_t>((nbt * L * 4 + 15) & ~15);
-    const uint32_t ebytes = static_cast<uint32_t>((nbt * 4 + 15) & ~15);
+    const uint32_t ebytes = H ? 0u : static_cast<uint32_t>((nbt * 4 + 15) & ~15);
     fence_proxy_async_smem();
     mbar_arrive_expect_tx(&full[s], (cbytes + ebytes) * cnt);
     for (int j = 0; j < cnt; ++j) {
       uint8_t* dst = stages + s * C::kStageBytes + j * C::kVecBytes;
       const int vec = v0 + j;
       bulk_g2s(dst, B.vals + (int64_t)vec * B.vstride + tb0 * L * 4, cbytes, &full[s]);
-      bulk_g2s(dst + C::kCodeBytes, reinterpret_cast<const uint8_t*>(B.exps) + (int64_t)vec * B.estride + tb0 * 4,
-               ebytes, &full[s]);
+      if (!H)
+        bulk_g2s(dst + C::kCodeBytes, reinterpret_cast<const uint8_t*>(B.exps) + (int64_t)vec * B.estride + tb0 * 4,
+                 ebytes, &full[s]);
     }
   };
   int issued = 0;  // thread 0 only
@@ -195,15 +231,43 @@ __global__ void __launch_bounds__(FDot<L>::kThreads) k_dot_frsz2(BasisView B, in
         double hp = 0.0;
         if (active && ok) {
           const uint8_t* st = stages + s * C::kStageBytes + j * C::kVecBytes;
-          const uint32_t e = reinterpret_cast<const uint32_t*>(st + C::kCodeBytes)[t];
+          const uint32_t* cw = reinterpret_cast<const uint32_t*>(st) + t * L;
           long long a1, a0;
-          block_dot<L>(reinterpret_cast<const uint32_t*>(st) + t * L, t, W1, W0, a1, a0);
-          // sum = (a1 2^27 + a0) 2^x with x = Ebar + Ew - 2096 - l, |a1 2^27 + a0| < 2^(l+57).
-          // Rounded to 2^(l-5) units it fits in 63 bits; the rounding error, at most 2^(l-6) units,
-          // is a quarter of the bound 2^-54 max|w| sum|vhat| of a block whose maxima are normal.
-          const long long th = (a1 << (32 - L)) + ((a0 + (1ll << (L - 6))) >> (L - 5));
-          const int x = (e > 1 ? static_cast<int>(e) : 1) + ew - 2096 - L;
-          hp = scale_pow2(static_cast<double>(th), x + L - 5);
+          if (!H) {
+            const uint32_t e = reinterpret_cast<const uint32_t*>(st + C::kCodeBytes)[t];
+            block_dot<L>(cw, t, W1, W0, a1, a0);
+            // sum = (a1 2^27 + a0) 2^x with x = Ebar + Ew - 2096 - l, |a1 2^27 + a0| < 2^(l+57).
+            // Rounded to 2^(l-5) units it fits in 63 bits; the rounding error, at most 2^(l-6)
+            // units, is a quarter of the bound 2^-54 max|w| sum|vhat| of a block whose maxima are
+            // normal.
+            const long long th = (a1 << (32 - L)) + ((a0 + (1ll << (L - 6))) >> (L - 5));
+            const int x = (e > 1 ? static_cast<int>(e) : 1) + ew - 2096 - L;
+            hp = scale_pow2(static_cast<double>(th), x + L - 5);
+          } else {
+            uint32_t emax = 0;
+            block_dot_fp16(cw, t, W1, W0, a1, a0, emax);
+            if (emax <= 15) {
+              // sum = (a1 2^27 + a0) 2^(ew - 1099) exactly (V in units of 2^-24, W in units of
+              // 2^(ew - 1075)); |a1| < 2^56, |a0| < 2^57. Kept exactly when |a1| < 2^35, else
+              // rounded to 2^u units with u chosen so that 62 bits of the sum remain.
+              const unsigned long long A = static_cast<unsigned long long>(a1 < 0 ? -a1 : a1);
+              const int bl = 64 - __clzll(static_cast<long long>(A));
+              const int u = bl > 35 ? bl - 35 : 0;
+              const long long th = u == 0 ? (a1 << 27) + a0 : (a1 << (27 - u)) + ((a0 + (1ll << (u - 1))) >> u);
+              hp = scale_pow2(static_cast<double>(th), u + ew - 1099);
+            } else {
+              // a value of magnitude >= 2 in the block (not a Krylov vector): the FP64 dot of the
+              // decoded values with w, read again from memory
+              const uint16_t* hv = reinterpret_cast<const uint16_t*>(cw);
+              const double* wb = w + b * 32;
+              const int64_t rem = B.n - b * 32;
+              double acc = 0.0;
+#pragma unroll 1
+              for (int k = 0; k < 32; ++k)
+                if (k < rem) acc = fma(widen_f16(hv[k]), __ldg(wb + k), acc);
+              hp = acc;
+            }
+          }
         }
         myred[(vj % C::kBatch) * C::kRedStride + lane] = hp;
         if (vj % C::kBatch == C::kBatch - 1 || vj == nv - 1) {
@@ -262,6 +326,23 @@ __global__ void __launch_bounds__(FDot<L>::kThreads) k_dot_frsz2(BasisView B, in
   }
 }
 
+template <int L>
+__global__ void __launch_bounds__(FDot<L>::kThreads) k_dot_frsz2(BasisView B, int nvec, const double* __restrict__ w,
+                                                                 double* __restrict__ out,
+                                                                 double* __restrict__ partials,
+                                                                 unsigned int* counter, int* err, Gate gate) {
+  dot_body<L, false>(B, nvec, w, out, partials, counter, err, gate);
+}
+
+// The binary16 basis (two resident CTAs of 256 threads: registers capped at 128).
+__global__ void __launch_bounds__(FDot<16, true>::kThreads, 2) k_dot_fp16(BasisView B, int nvec,
+                                                                          const double* __restrict__ w,
+                                                                          double* __restrict__ out,
+                                                                          double* __restrict__ partials,
+                                                                          unsigned int* counter, int* err, Gate gate) {
+  dot_body<16, true>(B, nvec, w, out, partials, counter, err, gate);
+}
+
 // ================================================================================================
 // update: 8 consecutive values per thread, 4 threads per block, 32 blocks per tile (64 at l = 16),
 // four basis vectors per pipeline stage, vectors in groups of at most 32 (the exact integer sums
@@ -271,12 +352,37 @@ __global__ void __launch_bounds__(FDot<L>::kThreads) k_dot_frsz2(BasisView B, in
 // S pipeline stages of 4 vectors: 2 when the grid fills the GPU (occupancy matters); 12 when it
 // does not (small n: each CTA then has little work per stage, and only more copies in flight hide
 // the latency).
-template <int L, int S = 2>
+// Shape of the full-grid update per code width (threads, resident CTAs the registers are capped
+// for); the defaults are the measured best, settable at build time (-DCBG_UPD_<knob>_<l>=...).
+#ifndef CBG_UPD_THREADS_16
+#define CBG_UPD_THREADS_16 256
+#endif
+#ifndef CBG_UPD_THREADS_21
+#define CBG_UPD_THREADS_21 128
+#endif
+#ifndef CBG_UPD_THREADS_32
+#define CBG_UPD_THREADS_32 128
+#endif
+#ifndef CBG_UPD_MINB_16
+#define CBG_UPD_MINB_16 3
+#endif
+#ifndef CBG_UPD_MINB_21
+#define CBG_UPD_MINB_21 4
+#endif
+#ifndef CBG_UPD_MINB_32
+#define CBG_UPD_MINB_32 4
+#endif
+#ifndef CBG_UPD_STAGES
+#define CBG_UPD_STAGES 2
+#endif
+
+template <int L, int S = CBG_UPD_STAGES>
 struct FUpd {
   // 128 threads and 32-block tiles (4 KB of l = 32 codes per vector and stage); at l = 16, 256
   // threads and 64-block tiles, whose larger copies measured 2.7% faster there (and 2.3% slower at
   // l = 32); the deep pipeline keeps 128
-  static constexpr int kThreads = (S != 12 && L == 16) ? 256 : 128;
+  static constexpr int kThreads =
+      S == 12 ? 128 : (L == 16 ? CBG_UPD_THREADS_16 : (L == 21 ? CBG_UPD_THREADS_21 : CBG_UPD_THREADS_32));
   static constexpr int kWarps = kThreads / 32;
   static constexpr int kBlocks = kThreads / 4;
   static constexpr int kVps = 4;  // basis vectors per stage
@@ -285,7 +391,8 @@ struct FUpd {
   // resident CTAs per SM the register allocation is capped for (measured per code width: l = 16,
   // at 256 threads, with a few spills at 3; l = 21 with 4; l = 32 runs 4 by shared memory and uses
   // the registers for an early load of w); the deep pipeline runs one CTA per SM
-  static constexpr int kMinBlocks = S == 12 ? 1 : (L == 32 ? 4 : (L == 21 ? 4 : 3));
+  static constexpr int kMinBlocks =
+      S == 12 ? 1 : (L == 32 ? CBG_UPD_MINB_32 : (L == 21 ? CBG_UPD_MINB_21 : CBG_UPD_MINB_16));
   static constexpr int kVecBytes = kBlocks * L * 4;
   static constexpr int kStageBytes = kVps * kVecBytes;
   // dynamic smem: stages | coefficient table [kGroup][kBlocks] (int2) | exponent words of one group
@@ -332,13 +439,17 @@ __device__ __forceinline__ void load_codes8(const uint32_t* st, int t, uint32_t 
   }
 }
 
-template <int L, int SD>
-__global__ void __launch_bounds__(FUpd<L, SD>::kThreads, FUpd<L, SD>::kMinBlocks) k_update_frsz2(BasisView B, int nvec_arg, const int* nvec_dev,
-                                                                    const double* __restrict__ hcoef, int negate,
-                                                                    double* __restrict__ w,
-                                                                    double* __restrict__ partials,
-                                                                    unsigned int* counter, int* err, NormEpilogue epi,
-                                                                    Gate gate) {
+// H: the basis is stored as binary16 in the l = 16 layout, without exponent words. Its values below 2
+// are exact integers in units of 2^-24 (fp16_fixed), i.e. codes of a block with the fixed exponent
+// 1023 and LE = 26 code bits; a vector holding a larger value in a thread's range is subtracted by
+// that warp in FP64 instead (global read-modify-write of w, which the tile's end then reads).
+template <int L, int SD, bool H>
+__device__ __forceinline__ void update_body(const BasisView& B, int nvec_arg, const int* nvec_dev,
+                                            const double* __restrict__ hcoef, int negate, double* __restrict__ w,
+                                            double* __restrict__ partials, unsigned int* counter, int* err,
+                                            const NormEpilogue& epi, const Gate& gate) {
+  static_assert(!H || L == 16, "binary16 blocks have the l = 16 layout");
+  constexpr int LE = H ? 26 : L;  // code bits, sign included
   using C = FUpd<L, SD>;
   constexpr int T = C::kThreads, NBT = C::kBlocks, G = C::kGroup, S = C::kStages, VPS = C::kVps;
   if (gate_skip(gate)) return;
@@ -375,10 +486,10 @@ __global__ void __launch_bounds__(FUpd<L, SD>::kThreads, FUpd<L, SD>::kMinBlocks
     hexp[i] = e > 1 ? e : 1;
   }
   // The group sums are kept in units of 2^(sh) against their block scale, sh = l - 5 + gb, so
-  // that up to 2^gb of them add up in 63 bits.
+  // that up to 2^gb of them add up in 63 bits (binary16: sh from the sums' actual size, below).
   const int ngroups = (nvec + G - 1) / G;
   const int gb = ngroups > 1 ? 32 - __clz(ngroups - 1) : 0;
-  const int sh = L - 5 + gb;
+  const int sh_fixed = L - 5 + gb;
   if (t == 0) {
     for (int s = 0; s < S; ++s) {
       mbar_init(&full[s], 1);
@@ -419,7 +530,7 @@ __global__ void __launch_bounds__(FUpd<L, SD>::kThreads, FUpd<L, SD>::kMinBlocks
                ebytes, &ebar[0]);
   };
   int issued = 0, eissued = 0;  // warp 0: code copies (thread 0) and exponent-group copies issued
-  if (warp == 0 && ntiles > 0 && nvec > 0) {
+  if (!H && warp == 0 && ntiles > 0 && nvec > 0) {
     issue_exps(0, 0);
     ++eissued;
   }
@@ -454,11 +565,11 @@ __global__ void __launch_bounds__(FUpd<L, SD>::kThreads, FUpd<L, SD>::kMinBlocks
         wpre[2 * i + 1] = v.y;
       }
     }
-    // sum over the groups so far, in units of 2^(rc - 2101 + gb)
+    // sum over the groups so far, in units of 2^xc
     long long tacc[8];
 #pragma unroll
     for (int k = 0; k < 8; ++k) tacc[k] = 0;
-    int rc = 0;
+    int xc = 0;
     for (int g0 = 0; g0 < nvec; g0 += G) {
       const int gn = min(G, nvec - g0);
       __syncthreads();  // the previous group's coefficient table is no longer read
@@ -466,11 +577,14 @@ __global__ void __launch_bounds__(FUpd<L, SD>::kThreads, FUpd<L, SD>::kMinBlocks
         aborted = true;
         break;
       }
-      const bool eok = mbar_wait_bounded(&ebar[0], static_cast<uint32_t>(egroups & 1));
-      ++egroups;
-      if (!eok) {
-        flags[0] = 1;
-        atomicOr(err, kDevErrTimeout);
+      bool eok = true;
+      if (!H) {
+        eok = mbar_wait_bounded(&ebar[0], static_cast<uint32_t>(egroups & 1));
+        ++egroups;
+        if (!eok) {
+          flags[0] = 1;
+          atomicOr(err, kDevErrTimeout);
+        }
       }
       // rexp = max over the group of (Eh_i + Ebar_{i,b}): exponent of the block's largest term;
       // the 4 threads of a block split the group's vectors and combine with shuffles.
@@ -479,7 +593,7 @@ __global__ void __launch_bounds__(FUpd<L, SD>::kThreads, FUpd<L, SD>::kMinBlocks
 #pragma unroll
       for (int kk = 0; kk < G / 4; ++kk) {
         const int v = q + 4 * kk;
-        const uint32_t e = (v < gn && active && eok) ? exq[v * NBT + blk] : 0u;
+        const uint32_t e = H ? 1023u : ((v < gn && active && eok) ? exq[v * NBT + blk] : 0u);
         ev[kk] = e;
         if (v < gn) r = max(r, hexp[g0 + v] + (e > 1 ? static_cast<int>(e) : 1));
       }
@@ -501,7 +615,7 @@ __global__ void __launch_bounds__(FUpd<L, SD>::kThreads, FUpd<L, SD>::kMinBlocks
       }
       __syncthreads();
       // the exponent words of the next group arrive while this group is processed
-      if (warp == 0 && !flag_read(&flags[0])) {
+      if (!H && warp == 0 && !flag_read(&flags[0])) {
         if (g0 + G < nvec) {
           issue_exps(tile, g0 + G);
           ++eissued;
@@ -536,7 +650,7 @@ __global__ void __launch_bounds__(FUpd<L, SD>::kThreads, FUpd<L, SD>::kMinBlocks
             }
           }
         }
-        if (active && ok) {
+        if (!H && active && ok) {
           const uint8_t* st = stages + s * C::kStageBytes;
 #pragma unroll
           for (int j = 0; j < VPS; ++j) {
@@ -549,6 +663,35 @@ __global__ void __launch_bounds__(FUpd<L, SD>::kThreads, FUpd<L, SD>::kMinBlocks
                 const int32_t sv = code_to_int<L>(c[k]);
                 mac_wide(acc0[k], sv, gp.x);
                 mac_wide(acc1[k], sv, gp.y);
+              }
+            }
+          }
+        }
+        if (H && ok) {  // every lane takes part: the warp decides together which path a vector takes
+          const uint8_t* st = stages + s * C::kStageBytes;
+#pragma unroll
+          for (int j = 0; j < VPS; ++j) {
+            if (v + j < gn) {
+              uint32_t c[8];
+              load_codes8<L>(reinterpret_cast<const uint32_t*>(st + j * C::kVecBytes), t, c);
+              uint32_t emax = 0;
+              int32_t sv[8];
+#pragma unroll
+              for (int k = 0; k < 8; ++k) sv[k] = fp16_fixed(c[k], emax);
+              if (!__any_sync(0xffffffffu, active && emax > 15)) {
+                if (active) {
+                  const int2 gp = gam[(v + j) * NBT + blk];
+#pragma unroll
+                  for (int k = 0; k < 8; ++k) {
+                    mac_wide(acc0[k], sv[k], gp.x);
+                    mac_wide(acc1[k], sv[k], gp.y);
+                  }
+                }
+              } else if (active) {  // a value of magnitude >= 2 (not a Krylov vector): FP64
+                const double hv = negate ? -hcoef[g0 + v + j] : hcoef[g0 + v + j];
+#pragma unroll 1
+                for (int k = 0; k < 8; ++k)
+                  if (k0 + k < B.n) w[k0 + k] = fma(-hv, widen_f16(c[k]), w[k0 + k]);
               }
             }
           }
@@ -568,8 +711,25 @@ __global__ void __launch_bounds__(FUpd<L, SD>::kThreads, FUpd<L, SD>::kMinBlocks
         // to units of 2^sh (at most 2^(gb-58) of the block's largest possible term, 2^(l+52) units):
         // |th| < 2^(62-gb). It joins the running sum at the larger of the two block scales; every
         // rescaling rounds to nearest, again at most 2^(gb-58) of the larger largest term.
+        // binary16: the largest of the thread's sums sets the unit, keeping 61 - gb bits of it (its
+        // codes are far below their bound 2^25 for the small values of a Krylov vector)
+        int sh = sh_fixed;
+        if (H) {
+          unsigned long long o1 = 0, o0 = 0;
+#pragma unroll
+          for (int k = 0; k < 8; ++k) {
+            o1 |= static_cast<unsigned long long>(acc1[k] < 0 ? -acc1[k] : acc1[k]);
+            o0 |= static_cast<unsigned long long>(acc0[k] < 0 ? -acc0[k] : acc0[k]);
+          }
+          const int bl = max(o1 ? 64 - __clzll(static_cast<long long>(o1)) + 27 : 0,
+                             64 - __clzll(static_cast<long long>(o0)));
+          sh = max(0, bl - (61 - gb));
+        }
         long long th[8];
-        if (sh <= 27) {
+        if (sh == 0) {
+#pragma unroll
+          for (int k = 0; k < 8; ++k) th[k] = (acc1[k] << 27) + acc0[k];
+        } else if (sh <= 27) {
 #pragma unroll
           for (int k = 0; k < 8; ++k) th[k] = (acc1[k] << (27 - sh)) + ((acc0[k] + (1ll << (sh - 1))) >> sh);
         } else {
@@ -580,14 +740,16 @@ __global__ void __launch_bounds__(FUpd<L, SD>::kThreads, FUpd<L, SD>::kMinBlocks
             th[k] = (x + (y >> 27)) >> (sh - 27);
           }
         }
-        if (g0 == 0 || r >= rc) {
-          const int dd = g0 == 0 ? 0 : r - rc;
+        // th is in units of 2^xg (sum_i s G in units of 2^(rexp - 2096 - LE))
+        const int xg = r - 2096 - LE + sh;
+        if (g0 == 0 || xg >= xc) {
+          const int dd = g0 == 0 ? 0 : xg - xc;
 #pragma unroll
           for (int k = 0; k < 8; ++k) tacc[k] = round_shift_right(tacc[k], dd) + th[k];
-          rc = r;
+          xc = xg;
         } else {
 #pragma unroll
-          for (int k = 0; k < 8; ++k) tacc[k] += round_shift_right(th[k], rc - r);
+          for (int k = 0; k < 8; ++k) tacc[k] += round_shift_right(th[k], xc - xg);
         }
       }
     }
@@ -595,7 +757,7 @@ __global__ void __launch_bounds__(FUpd<L, SD>::kThreads, FUpd<L, SD>::kMinBlocks
     // value k: w_k - tacc_k 2^x, one conversion and one fused multiply-add (the product tv 2^x is
     // exact in the normal range, so the FMA rounds exactly like the subtraction of the product)
     double tv[8];
-    const int x = rc - 2101 + gb;
+    const int x = xc;
     const bool xnorm = x >= -1022 && x <= 1023;
     const double p2 = -pow2_normal(xnorm ? x : 0);
 #pragma unroll
@@ -665,6 +827,22 @@ __global__ void __launch_bounds__(FUpd<L, SD>::kThreads, FUpd<L, SD>::kMinBlocks
   }
 }
 
+template <int L, int SD>
+__global__ void __launch_bounds__(FUpd<L, SD>::kThreads, FUpd<L, SD>::kMinBlocks)
+    k_update_frsz2(BasisView B, int nvec_arg, const int* nvec_dev, const double* __restrict__ hcoef, int negate,
+                   double* __restrict__ w, double* __restrict__ partials, unsigned int* counter, int* err,
+                   NormEpilogue epi, Gate gate) {
+  update_body<L, SD, false>(B, nvec_arg, nvec_dev, hcoef, negate, w, partials, counter, err, epi, gate);
+}
+
+template <int SD>
+__global__ void __launch_bounds__(FUpd<16, SD>::kThreads, FUpd<16, SD>::kMinBlocks)
+    k_update_fp16(BasisView B, int nvec_arg, const int* nvec_dev, const double* __restrict__ hcoef, int negate,
+                  double* __restrict__ w, double* __restrict__ partials, unsigned int* counter, int* err,
+                  NormEpilogue epi, Gate gate) {
+  update_body<16, SD, true>(B, nvec_arg, nvec_dev, hcoef, negate, w, partials, counter, err, epi, gate);
+}
+
 // ================================================================================================
 // launchers
 // ================================================================================================
@@ -675,6 +853,21 @@ const void* fnp(K k) {
   return reinterpret_cast<const void*>(k);
 }
 }  // namespace
+
+// The dot of a binary16 basis on the integer pipeline (FDot<16, true>).
+int fp16_dot_launch(const BasisView& B, int nvec, const double* w, double* out, double* partials,
+                    unsigned int* counter, int* err, const Gate& gate, int max_grid, cudaStream_t stream) {
+  using C = FDot<16, true>;
+  const void* fn = fnp(k_dot_fp16);
+  const size_t smem = C::smem_bytes(nvec);
+  int gx, full;
+  int st = basis_launch_config(fn, C::kThreads, smem, (B.n + 31) / 32, C::kThreads / 8, max_grid, &gx, &full);
+  if (st) return st;
+  const dim3 grid(gx, dot_vector_split(gx, full, nvec, max_grid));
+  k_dot_fp16<<<grid, C::kThreads, smem, stream>>>(B, nvec, w, out, partials, counter, err, gate);
+  cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? CBG_OK : cuda_fail(e, "fp16 dot launch");
+}
 
 int frsz2_dot_launch(const BasisView& B, int nvec, const double* w, double* out, double* partials,
                      unsigned int* counter, int* err, const Gate& gate, int max_grid, cudaStream_t stream) {
@@ -702,23 +895,26 @@ int frsz2_dot_launch(const BasisView& B, int nvec, const double* w, double* out,
 
 namespace {
 
-template <int L, int S>
+template <int L, int S, bool H>
 int frsz2_update_launch_t(const BasisView& B, int nvec, const int* nvec_dev, const double* h, int negate, double* w,
                           double* partials, unsigned int* counter, int* err, const NormEpilogue& epi,
                           const Gate& gate, int grid, cudaStream_t stream) {
-  const void* fn = fnp(k_update_frsz2<L, S>);
+  const void* fn = H ? fnp(k_update_fp16<S>) : fnp(k_update_frsz2<L, S>);
   const size_t smem = FUpd<L, S>::smem_bytes(nvec);
   int g;
   constexpr int T = FUpd<L, S>::kThreads;
   int st = basis_launch_config(fn, T, smem, (B.n + 31) / 32, T / 16, kMaxGrid, &g, nullptr);
   if (st) return st;
   if (grid > 0 && grid < g) g = grid;
-  k_update_frsz2<L, S><<<g, T, smem, stream>>>(B, nvec, nvec_dev, h, negate, w, partials, counter, err, epi, gate);
+  if (H)
+    k_update_fp16<S><<<g, T, smem, stream>>>(B, nvec, nvec_dev, h, negate, w, partials, counter, err, epi, gate);
+  else
+    k_update_frsz2<L, S><<<g, T, smem, stream>>>(B, nvec, nvec_dev, h, negate, w, partials, counter, err, epi, gate);
   cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? CBG_OK : cuda_fail(e, "frsz2 update launch");
 }
 
-template <int L>
+template <int L, bool H = false>
 int frsz2_update_launch_l(const BasisView& B, int nvec, const int* nvec_dev, const double* h, int negate, double* w,
                           double* partials, unsigned int* counter, int* err, const NormEpilogue& epi,
                           const Gate& gate, cudaStream_t stream) {
@@ -728,11 +924,20 @@ int frsz2_update_launch_l(const BasisView& B, int nvec, const int* nvec_dev, con
   // CTAs the blocks need (8 blocks at least per CTA): fewer than SMs means an underfilled GPU
   const int64_t need = ((B.n + 31) / 32 + 7) / 8;
   if (need < di.sms)
-    return frsz2_update_launch_t<L, 12>(B, nvec, nvec_dev, h, negate, w, partials, counter, err, epi, gate, 0, stream);
-  return frsz2_update_launch_t<L, 2>(B, nvec, nvec_dev, h, negate, w, partials, counter, err, epi, gate, 0, stream);
+    return frsz2_update_launch_t<L, 12, H>(B, nvec, nvec_dev, h, negate, w, partials, counter, err, epi, gate, 0,
+                                           stream);
+  return frsz2_update_launch_t<L, CBG_UPD_STAGES, H>(B, nvec, nvec_dev, h, negate, w, partials, counter, err, epi, gate,
+                                                     0, stream);
 }
 
 }  // namespace
+
+// The update of a binary16 basis on the integer pipeline (update_body<16, S, true>).
+int fp16_update_launch(const BasisView& B, int nvec, const int* nvec_dev, const double* h, int negate, double* w,
+                       double* partials, unsigned int* counter, int* err, const NormEpilogue& epi, const Gate& gate,
+                       cudaStream_t stream) {
+  return frsz2_update_launch_l<16, true>(B, nvec, nvec_dev, h, negate, w, partials, counter, err, epi, gate, stream);
+}
 
 int frsz2_update_launch(const BasisView& B, int nvec, const int* nvec_dev, const double* h, int negate, double* w,
                         double* partials, unsigned int* counter, int* err, const NormEpilogue& epi,

@@ -83,6 +83,44 @@ __device__ __forceinline__ void block_dot(const uint32_t* cw, int t, const int32
   a0 = a0e + a0o;
 }
 
+// A binary16 value (its bit pattern in bits 0-15) below 2 in magnitude as an exact integer in
+// units of 2^-24: m 2^(E-1) for a normal value (E the exponent field, m the significand with its
+// hidden bit), m for a subnormal one; |V| < 2^25. emax receives the largest exponent field seen: a
+// value with E > 15 (|v| >= 2) does not fit and its block is summed on the FP64 path instead.
+__device__ __forceinline__ int32_t fp16_fixed(uint32_t h, uint32_t& emax) {
+  const uint32_t e = (h >> 10) & 0x1Fu;
+  emax = max(emax, e);
+  const uint32_t m = (h & 0x3FFu) | (e != 0u ? 0x400u : 0u);
+  const uint32_t mag = m << (e != 0u ? e - 1u : 0u);
+  const uint32_t s = 0u - ((h >> 15) & 1u);  // 0 or all ones
+  return static_cast<int32_t>((mag ^ s) - s);
+}
+
+// Integer dot of one block of 32 binary16 values (64 bytes, the layout of an l = 16 block) with
+// the thread's W registers, in the order and with the bank rotation of block_dot<16>.
+__device__ __forceinline__ void block_dot_fp16(const uint32_t* cw, int t, const int32_t (&W1)[32],
+                                               const int32_t (&W0)[32], long long& a1, long long& a0,
+                                               uint32_t& emax) {
+  long long a1e = 0, a0e = 0, a1o = 0, a0o = 0;
+  const uint4* c4 = reinterpret_cast<const uint4*>(cw);
+#pragma unroll
+  for (int c = 0; c < 4; ++c) {
+    const uint4 q = c4[(c + (t >> 1)) & 3];
+    const uint32_t wv[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll
+    for (int h = 0; h < 4; ++h) {
+      const int32_t lo = fp16_fixed(wv[h], emax);
+      const int32_t hi = fp16_fixed(wv[h] >> 16, emax);
+      mac_wide(a1e, lo, W1[8 * c + 2 * h]);
+      mac_wide(a0e, lo, W0[8 * c + 2 * h]);
+      mac_wide(a1o, hi, W1[8 * c + 2 * h + 1]);
+      mac_wide(a0o, hi, W0[8 * c + 2 * h + 1]);
+    }
+  }
+  a1 = a1e + a1o;
+  a0 = a0e + a0o;
+}
+
 // Register slot r of the thread's W holds block value w_index(L, t, r) (the order block_dot reads).
 template <int L>
 __device__ __forceinline__ int w_index(int t, int r) {

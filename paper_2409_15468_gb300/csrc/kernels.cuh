@@ -74,6 +74,11 @@ int basis_launch_config(const void* fn, int threads, size_t smem, int64_t units,
 int dot_vector_split(int gx, int full, int nvec, int max_grid);
 int frsz2_dot_launch(const BasisView& B, int nvec, const double* w, double* out, double* partials,
                      unsigned int* counter, int* err, const Gate& gate, int max_grid, cudaStream_t stream);
+int fp16_dot_launch(const BasisView& B, int nvec, const double* w, double* out, double* partials,
+                    unsigned int* counter, int* err, const Gate& gate, int max_grid, cudaStream_t stream);
+int fp16_update_launch(const BasisView& B, int nvec, const int* nvec_dev, const double* h, int negate, double* w,
+                       double* partials, unsigned int* counter, int* err, const NormEpilogue& epi, const Gate& gate,
+                       cudaStream_t stream);
 int frsz2_update_launch(const BasisView& B, int nvec, const int* nvec_dev, const double* h, int negate, double* w,
                         double* partials, unsigned int* counter, int* err, const NormEpilogue& epi,
                         const Gate& gate, cudaStream_t stream);
@@ -103,14 +108,21 @@ int launch_frsz2_decompress(const uint32_t* exps, const uint32_t* codes, int64_t
 int launch_load(const BasisView& B, int slot, double* dst, cudaStream_t stream);
 
 // ---- spmv.cu ------------------------------------------------------------------------------------
+// The rows of a matrix with long rows in a stable order by length bucket: perm (n rows) and the
+// scratch of launch_row_order, whose front holds where each bucket starts.
+struct RowOrder {
+  const int32_t* perm;
+  const int32_t* scratch;
+};
 // y = A x (or y = bsub - A x when bsub is not null); ||y||^2 to the epilogue. partials: kMaxGrid.
+// A matrix with long rows (spmv_lanes_per_row > 1) needs its row order.
 int launch_spmv(int n, int64_t nnz, const int32_t* row_ptr, const int32_t* col, const double* vals, const double* x,
-                double* y, const double* bsub, const int32_t* perm, double* partials, unsigned int* counter, int* err,
-                const NormEpilogue& epi, const Gate& gate, cudaStream_t stream);
-// Lanes per row of the SpMV for this matrix shape (1: one thread per row, which ignores perm).
+                double* y, const double* bsub, const RowOrder* order, double* partials, unsigned int* counter,
+                int* err, const NormEpilogue& epi, const Gate& gate, cudaStream_t stream);
+// Lanes per row of the SpMV for this matrix shape (1: one thread per row, which needs no row order).
 int spmv_lanes_per_row(int n, int64_t nnz);
 // perm := the rows in a stable order by length bucket (see spmv.cu); scratch holds
-// row_order_scratch_bytes(n) bytes.
+// row_order_scratch_bytes(n) bytes and keeps the bucket starts for the SpMV.
 size_t row_order_scratch_bytes(int n);
 int launch_row_order(int n, const int32_t* row_ptr, int32_t* perm, int32_t* scratch, cudaStream_t stream);
 // dinv := 1 / diag(A) (kDevErrBadDiagonal on a zero or missing entry); x += d .* z.

@@ -38,6 +38,25 @@ def make_basis(cbg, orc, n, nvec, fmt, l, seed):
     return B, Vhat, exps
 
 
+def fp16_update_tolerance(Vhat, h, w, idx):
+    """Error bound of the binary16 update (exact integer products of the stored values, exact in
+    units of 2^-24, with h_i as 54-bit fixed point against the largest |h| of its group of 32
+    vectors): the coefficients' rounding adds at most 2^-53 max|h| sum_i |vhat_ik|; each group
+    sum keeps 61 - gb bits of the largest of the thread's 8 sums (elements 8c .. 8c + 7), at most
+    2^-55 max|h| max_{k' in the 8} sum_i |vhat_ik'| per rounding for up to 2^6 groups; the final
+    conversion and subtraction add 2^-52 (|w_k| + sum_i |vhat_ik h_i|). With a factor-4 margin."""
+    n = w.size
+    absv = np.abs(Vhat)
+    col = absv.sum(axis=0)  # sum_i |vhat_ik|
+    pad = np.zeros(((n + 7) // 8) * 8)
+    pad[:n] = col
+    chunk = pad.reshape(-1, 8).max(axis=1)[idx // 8]
+    hmax = np.abs(h).max()
+    terms = (absv[:, idx] * np.abs(h)[:, None]).sum(axis=0)
+    return 4 * (2.0 ** -50 * (np.abs(w[idx]) + terms) + 2.0 ** -53 * hmax * col[idx] +
+                2.0 ** -52 * hmax * chunk) + 1e-300
+
+
 def dot_tolerance(Vhat, w):
     n = w.size
     nb = (n + 31) // 32
@@ -87,6 +106,8 @@ def test_update(cbg, orc, fmt, l, n, nvec):
     else:
         tmax = terms.max(axis=0)
     tol = 4 * (2.0 ** -50 * (np.abs(w[idx]) + terms.sum(axis=0)) + nvec * 2.0 ** -53 * tmax) + 1e-300
+    if fmt == 2:
+        tol = fp16_update_tolerance(Vhat, h, w, idx)
     err = np.abs(out[idx] - ref)
     assert np.all(err <= tol), (err / tol).max()
     # the fused norm is ||w||^2 of the updated vector
@@ -183,3 +204,42 @@ def test_empty_inputs(cbg, orc, fmt, l):
     torch.cuda.synchronize()
     assert h[:3].tolist() == [0.0, 0.0, 0.0] and h[3].item() == 7.0
     assert nrm.item() == 0.0
+
+
+@pytest.mark.parametrize("op", ["dot", "update"])
+def test_fp16_values_of_two_and_more(cbg, orc, op):
+    """A binary16 basis whose vectors are not normalised (values up to ~1000): the integer path takes
+    values below 2 only (exact integers in units of 2^-24); a block (dot) or a warp's range of a
+    vector (update) holding a larger value goes through FP64 products instead. Mixed with unit-norm
+    vectors, against the oracle."""
+    n, nvec = 20000 + 13, 12
+    B, Vhat, _ = make_basis(cbg, orc, n, nvec, 2, 32, seed=77)
+    rng = np.random.default_rng(78)
+    scale = np.where(np.arange(nvec) % 3 == 0, 300.0, 1.0)  # every third vector reaches values >= 2
+    V = workloads.basis_values(nvec, n, seed=79).numpy()
+    V /= np.abs(V).max(axis=1, keepdims=True)
+    V *= scale[:, None]
+    Vd = torch.from_numpy(V).cuda()
+    for i in range(nvec):
+        B.store(i, Vd[i].contiguous())
+    enc = [orc.encode(V[i], 2, 32) for i in range(nvec)]
+    Vhat = np.stack([orc.decode(v, e, n, 2, 32) for v, e in enc])
+    assert np.abs(Vhat).max() >= 2.0 and np.abs(Vhat[1]).max() < 2.0
+    if op == "dot":
+        w = rng.standard_normal(n)
+        got = B.dot(nvec, torch.from_numpy(w).cuda()).cpu().numpy()
+        ref = orc.basis_dot(Vhat, w)
+        tol = dot_tolerance(Vhat, w)
+        assert np.all(np.abs(got - ref) <= tol), (np.abs(got - ref) / tol).max()
+    else:
+        w = rng.standard_normal(n)
+        h = rng.standard_normal(nvec) * np.exp2(rng.integers(-10, 3, nvec))
+        wd = torch.from_numpy(w).cuda()
+        B.update(nvec, torch.from_numpy(h).cuda(), wd)
+        out = wd.cpu().numpy()
+        ref = orc.basis_update(Vhat, h, w)
+        idx = np.arange(n)
+        terms = np.abs(Vhat * h[:, None])
+        # the FP64 path's bound (the cast formats') added to the integer path's
+        tol = fp16_update_tolerance(Vhat, h, w, idx) + 4 * nvec * 2.0 ** -53 * terms.sum(axis=0)
+        assert np.all(np.abs(out - ref) <= tol), (np.abs(out - ref) / tol).max()
