@@ -188,8 +188,9 @@ int cbg_csr_validate(int32_t n, int64_t nnz, const int32_t* d_row_ptr, const int
 /* d_y = A d_x for the CSR matrix (int32 row pointers and columns, FP64 values): Fig. 1 step 3,
  * w := A M^{-1} v with M = I (no preconditioner: Solver Configuration). If d_norm2 is not NULL it
  * receives ||y||^2 (step 4). nnz = row_ptr[n]; it chooses the kernel (one thread per row for
- * short rows, 4 lanes per row when the mean row length is 12 or more) and must match the matrix.
- * d_work: cbg_spmv_work_bytes(n) bytes. */
+ * short rows; when the mean row length is 12 or more, segments of 512 rows sorted by length in
+ * shared memory, with 1 to 32 lanes per row by length) and must match the matrix. d_work:
+ * cbg_spmv_work_bytes(n) bytes, 256-byte aligned. */
 size_t cbg_spmv_work_bytes(int32_t n);
 int cbg_spmv(int32_t n, int64_t nnz, const int32_t* d_row_ptr, const int32_t* d_col, const double* d_vals,
              const double* d_x, double* d_y, double* d_norm2, void* d_work, size_t work_bytes, void* stream);

@@ -422,11 +422,15 @@ int cbg_spmv(int32_t n, int64_t nnz, const int32_t* d_row_ptr, const int32_t* d_
   int st = device_info(&di);
   if (st) return st;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (work_bytes < cbg_spmv_work_bytes(n)) {
+    set_error("cbg_spmv: work buffer too small: %zu bytes given, %zu needed", work_bytes, cbg_spmv_work_bytes(n));
+    return CBG_ERR_INVALID_ARG;
+  }
   Work w;
   st = take_work(d_work, work_bytes, 1, s, &w);
   if (st) return st;
   NormEpilogue epi{d_norm2, nullptr, kEpiNone};
-  return launch_spmv(n, nnz, d_row_ptr, d_col, d_vals, d_x, d_y, nullptr, nullptr, w.partials, w.counter, w.err, epi,
+  return launch_spmv(n, nnz, d_row_ptr, d_col, d_vals, d_x, d_y, nullptr, w.partials, w.counter, w.err, epi,
                      Gate{nullptr, nullptr}, s);
 }
 

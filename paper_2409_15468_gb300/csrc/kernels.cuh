@@ -108,23 +108,12 @@ int launch_frsz2_decompress(const uint32_t* exps, const uint32_t* codes, int64_t
 int launch_load(const BasisView& B, int slot, double* dst, cudaStream_t stream);
 
 // ---- spmv.cu ------------------------------------------------------------------------------------
-// The rows of a matrix with long rows in a stable order by length bucket: perm (n rows) and the
-// scratch of launch_row_order, whose front holds where each bucket starts.
-struct RowOrder {
-  const int32_t* perm;
-  const int32_t* scratch;
-};
 // y = A x (or y = bsub - A x when bsub is not null); ||y||^2 to the epilogue. partials: kMaxGrid.
-// A matrix with long rows (spmv_lanes_per_row > 1) needs its row order.
 int launch_spmv(int n, int64_t nnz, const int32_t* row_ptr, const int32_t* col, const double* vals, const double* x,
-                double* y, const double* bsub, const RowOrder* order, double* partials, unsigned int* counter,
-                int* err, const NormEpilogue& epi, const Gate& gate, cudaStream_t stream);
-// Lanes per row of the SpMV for this matrix shape (1: one thread per row, which needs no row order).
+                double* y, const double* bsub, double* partials, unsigned int* counter, int* err,
+                const NormEpilogue& epi, const Gate& gate, cudaStream_t stream);
+// Lanes per row of the SpMV for this matrix shape (1: one thread per row; else the long-row kernel).
 int spmv_lanes_per_row(int n, int64_t nnz);
-// perm := the rows in a stable order by length bucket (see spmv.cu); scratch holds
-// row_order_scratch_bytes(n) bytes and keeps the bucket starts for the SpMV.
-size_t row_order_scratch_bytes(int n);
-int launch_row_order(int n, const int32_t* row_ptr, int32_t* perm, int32_t* scratch, cudaStream_t stream);
 // dinv := 1 / diag(A) (kDevErrBadDiagonal on a zero or missing entry); x += d .* z.
 int launch_jacobi_diag(int n, const int32_t* row_ptr, const int32_t* col, const double* vals, double* dinv, int* err,
                        cudaStream_t stream);

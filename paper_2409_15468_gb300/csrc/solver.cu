@@ -223,8 +223,6 @@ struct cbg_ctx {
   BasisMut basis;
   double *v, *w, *H, *R, *cs, *sn, *g, *u, *y, *partials, *hist, *bnorm2;
   double *dinv, *z;  // Jacobi preconditioner: 1 / diag(A) and the restart's V y (null without)
-  int32_t *perm, *perm_scratch;  // SpMV row order by length (null when rows are short)
-  bool perm_ready;
   OnchipPlan oc;  // oc.cluster > 0: every cycle is one cluster launch (onchip.cu)
   SolverCtl* ctl;
   SolverCtl* ctl_host;  // pinned mirror
@@ -248,7 +246,7 @@ namespace {
 struct Layout {
   int64_t vstride, estride;
   size_t off_basis_vals, off_basis_exps, off_v, off_w, off_H, off_R, off_cs, off_sn, off_g, off_u, off_y,
-      off_partials, off_hist, off_ctl, off_bnorm2, off_dinv, off_z, off_perm, off_perm_scratch, total;
+      off_partials, off_hist, off_ctl, off_bnorm2, off_dinv, off_z, total;
 };
 
 // CBG_OK, CBG_ERR_UNIMPLEMENTED (an FRSZ2 code width in [2, 32] other than 16, 21 and 32) or
@@ -307,10 +305,6 @@ Layout layout_of(int32_t n, const cbg_opts* o) {
   const bool jac = o->precond == CBG_PRECOND_JACOBI;
   L.off_dinv = take(jac ? 8ll * n : 0);
   L.off_z = take(jac ? 8ll * n : 0);
-  // row order for the lanes-per-row SpMV: reserved for every matrix (about 4.2 bytes per row; the
-  // workspace size depends on n and the options only), used when the rows are long
-  L.off_perm = take(4ll * n);
-  L.off_perm_scratch = take(static_cast<int64_t>(row_order_scratch_bytes(n)));
   L.total = off;
   return L;
 }
@@ -361,7 +355,7 @@ int enqueue_readback(cbg_ctx* c) {
 // Residual r := b - A x into w with beta = ||r|| (step 1), then the control-block readback.
 int enqueue_residual(cbg_ctx* c) {
   NormEpilogue epi{nullptr, c->ctl, kEpiResidual};
-  int st = launch_spmv(c->n, c->nnz, c->row_ptr, c->col, c->vals, c->x, c->w, c->b, c->perm, c->partials,
+  int st = launch_spmv(c->n, c->nnz, c->row_ptr, c->col, c->vals, c->x, c->w, c->b, c->partials,
                        &c->ctl->counters[kCtrSpmv], &c->ctl->err, epi, Gate{nullptr, nullptr}, c->stream);
   if (st) return st;
   return enqueue_readback(c);
@@ -400,7 +394,7 @@ int enqueue_step(cbg_ctx* c, int j) {
   double* hcol = c->H + (size_t)j * ld;
   int st;
   NormEpilogue e_omega{nullptr, ctl, kEpiOmega};
-  st = launch_spmv(c->n, c->nnz, c->row_ptr, c->col, c->vals, c->v, c->w, nullptr, c->perm, c->partials,
+  st = launch_spmv(c->n, c->nnz, c->row_ptr, c->col, c->vals, c->v, c->w, nullptr, c->partials,
                    &ctl->counters[kCtrSpmv],
                    &ctl->err, e_omega, run, c->stream);
   if (st) return st;
@@ -600,10 +594,6 @@ int ctx_create_in(cbg_ctx** out, int32_t n, int64_t nnz, const int32_t* d_row_pt
   const bool jac = c->opts.precond == CBG_PRECOND_JACOBI;
   c->dinv = jac ? reinterpret_cast<double*>(base + L.off_dinv) : nullptr;
   c->z = jac ? reinterpret_cast<double*>(base + L.off_z) : nullptr;
-  const bool long_rows = spmv_lanes_per_row(n, nnz) > 1;
-  c->perm = long_rows ? reinterpret_cast<int32_t*>(base + L.off_perm) : nullptr;
-  c->perm_scratch = long_rows ? reinterpret_cast<int32_t*>(base + L.off_perm_scratch) : nullptr;
-  c->perm_ready = false;
   st = onchip_plan(n, nnz, &c->opts, &c->oc);
   if (st) {
     delete c;
@@ -772,11 +762,6 @@ int cbgmres_start(cbg_ctx* c, const double* d_b, double* d_x) {
   if (c->dinv) {  // M^{-1} = 1 / diag(A), after k_set_bnorm has cleared the error word
     st = launch_jacobi_diag(c->n, c->row_ptr, c->col, c->vals, c->dinv, &c->ctl->err, c->stream);
     if (st) return ctx_fail(c, st);
-  }
-  if (c->perm && !c->perm_ready) {  // once per context: the matrix is immutable while borrowed
-    st = launch_row_order(c->n, c->row_ptr, c->perm, c->perm_scratch, c->stream);
-    if (st) return ctx_fail(c, st);
-    c->perm_ready = true;
   }
   e = cudaMemcpyAsync(c->bnorm2_host, c->bnorm2, 8, cudaMemcpyDeviceToHost, c->stream);
   if (e != cudaSuccess) return ctx_fail(c, cuda_fail(e, "bnorm copy"));

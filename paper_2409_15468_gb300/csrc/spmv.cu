@@ -6,8 +6,17 @@
 // One thread per row for short rows: the stencil matrices have ~7 nonzeros per row, so the rows of a
 // warp cover a contiguous stretch of the value and column arrays that L1 serves to the per-nonzero
 // loads, and the FP64 work is exactly one FMA per nonzero (GB300's FP64 rate is the other bound of
-// this kernel). Matrices with long rows (mean >= 12 nonzeros) use 4 lanes per row instead.
-// Rows are strided over a grid sized to the SM count so that the norm partials stay few.
+// this kernel). Rows are strided over a grid sized to the SM count so that the norm partials stay
+// few.
+//
+// Matrices with long rows (mean >= 12 nonzeros, e.g. power-law row lengths): a CTA takes 512
+// consecutive rows, sorts them in shared memory by length bucket (floor(log2 len) + 1) and gives
+// each bucket its own number G of lanes per row, about 8-16 nonzeros per lane. A warp then serves
+// 32/G rows of lengths within a factor of two, so few lanes idle while it iterates to its longest
+// row (GB300 issues every FP64 warp instruction at full cost, whatever its active lanes), the row
+// sum costs log2(G) shuffle-adds, and the rows of a segment are read close together in time, so the
+// sectors that neighbouring rows share come from DRAM once (a global sort by length scattered them:
+// 1.47x the algorithmic DRAM bytes).
 #include "common.cuh"
 #include "kernels.cuh"
 
@@ -58,74 +67,140 @@ __global__ void __launch_bounds__(256) k_spmv(int n, const int32_t* __restrict__
   }
 }
 
-// Rows with many nonzeros (power-law matrices): G consecutive lanes per row, so the loads of a
-// row's values and column indices are coalesced and a long row is split G ways. Each lane issues
-// U independent (column, value, x-gather) loads before it uses any of them, and the next row's
-// bounds are loaded before the current row is processed, so several gathers are in flight per
-// lane. Each lane keeps one FMA chain and the G lanes of a row combine in a fixed shuffle order
-// (deterministic): on GB300 every extra FP64 add costs as much issue time as a gather, so the
-// combining work is kept to log2(G) adds per row and lane.
+// ---- long rows: segment-local sort by length, lanes per row by length -------------------------
+// Loads in flight per lane and resident CTAs per SM of the long-row kernel (measured best; settable
+// at build time for a sweep).
+#ifndef CBG_SPMV_LOADS
+#define CBG_SPMV_LOADS 8
+#endif
+#ifndef CBG_SPMV_CTAS_PER_SM
+#define CBG_SPMV_CTAS_PER_SM 8
+#endif
+constexpr int kRowBuckets = 12;  // floor(log2 len) + 1, capped: bucket 0 holds the empty rows
+constexpr int kSeg = 512;        // rows a CTA sorts and serves at a time
+
+// Lanes per row for rows of bucket b (lengths [2^(b-1), 2^b)): about 8-16 nonzeros per lane, at
+// most a warp per row.
+__device__ __forceinline__ int bucket_lanes(int b) {
+  const int g = b >= 5 ? 1 << (b - 4) : 1;
+  return g < 32 ? g : 32;
+}
+
+// The sum of a row over G consecutive lanes (sub = lane % G): each lane keeps U independent
+// (column, value, x-gather) loads in flight before its FMAs, one FMA chain per lane, and the G lanes
+// combine in a fixed shuffle order (deterministic).
 template <int G, int U>
-__global__ void __launch_bounds__(256) k_spmv_vec(int n, const int32_t* __restrict__ row_ptr,
+__device__ __forceinline__ double row_sum(int p0, int p1, int sub, const int32_t* __restrict__ col,
+                                          const double* __restrict__ vals, const double* __restrict__ x) {
+  double s = 0.0;
+  for (int p = p0 + sub; p < p1; p += G * U) {
+    int c[U];
+    double v[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int q = p + u * G;
+      c[u] = q < p1 ? __ldg(col + q) : -1;
+      v[u] = q < p1 ? __ldg(vals + q) : 0.0;
+    }
+    double xv[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) xv[u] = c[u] >= 0 ? __ldg(x + c[u]) : 0.0;
+#pragma unroll
+    for (int u = 0; u < U; ++u) s = fma(v[u], xv[u], s);
+  }
+#pragma unroll
+  for (int o = G / 2; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  return s;
+}
+
+// A CTA serves segments of kSeg rows (grid-strided): the segment's row pointers go to shared
+// memory, its rows are ordered by bucket there (within a bucket in any order: each row's sum does
+// not depend on it), and warps take work groups of 32/G rows of one bucket in turn. ||y||^2 is
+// then summed over the segment in row order, so it is deterministic.
+template <int U>
+__global__ void __launch_bounds__(256) k_spmv_seg(int n, const int32_t* __restrict__ row_ptr,
                                                   const int32_t* __restrict__ col, const double* __restrict__ vals,
                                                   const double* __restrict__ x, double* __restrict__ y,
-                                                  const double* __restrict__ bsub, const int32_t* __restrict__ perm,
-                                                  double* __restrict__ partials, unsigned int* counter, int* err,
-                                                  NormEpilogue epi, Gate gate) {
+                                                  const double* __restrict__ bsub, double* __restrict__ partials,
+                                                  unsigned int* counter, int* err, NormEpilogue epi, Gate gate) {
   if (gate_skip_s(gate)) return;
+  __shared__ int srp[kSeg + 1];
+  __shared__ uint16_t sorder[kSeg];
+  __shared__ int cnt[kRowBuckets], fill[kRowBuckets], off[kRowBuckets + 1], gst[kRowBuckets + 1];
   __shared__ double red[8];
   __shared__ int flag;
+  constexpr int T = 256, PER = kSeg / T;
   const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
-  const int sub = lane & (G - 1);
-  // position j of the row order holds row perm[j] (rows sorted by length bucket, so the rows a
-  // warp handles together have similar lengths), or row j without a permutation
-  auto row_at = [&](int64_t j) -> int64_t { return perm ? static_cast<int64_t>(__ldg(perm + j)) : j; };
   double nrm = 0.0;
-  const int64_t groups = (int64_t)gridDim.x * (blockDim.x / G);
-  const int64_t g0 = (int64_t)blockIdx.x * (blockDim.x / G) + t / G;
-  // every lane of a warp runs the same number of row iterations (rows past n are empty), so the
-  // shuffles below always see the whole warp
-  const int64_t rows_per_group = ((int64_t)n + groups - 1) / groups;
-  int p0 = 0, p1 = 0;
-  int64_t i = g0 < n ? row_at(g0) : n;
-  if (g0 < n) {
-    p0 = __ldg(row_ptr + i);
-    p1 = __ldg(row_ptr + i + 1);
-  }
-  for (int64_t k = 0; k < rows_per_group; ++k) {
-    const int64_t jnext = g0 + (k + 1) * groups;
-    const int64_t inext = jnext < n ? row_at(jnext) : n;
-    int q0 = 0, q1 = 0;
-    if (inext < n) {
-      q0 = __ldg(row_ptr + inext);
-      q1 = __ldg(row_ptr + inext + 1);
+  const int nseg = (n + kSeg - 1) / kSeg;
+  for (int sg = blockIdx.x; sg < nseg; sg += gridDim.x) {
+    const int r0 = sg * kSeg, rows = min(kSeg, n - r0);
+    __syncthreads();  // the previous segment's shared arrays are no longer read
+    if (t < kRowBuckets) {
+      cnt[t] = 0;
+      fill[t] = 0;
     }
-    double s = 0.0;  // one chain: the loads of a pass are in flight before its first FMA
-    for (int p = p0 + sub; p < p1; p += G * U) {
-      int c[U];
-      double v[U];
+    for (int i = t; i <= rows; i += T) srp[i] = __ldg(row_ptr + r0 + i);
+    __syncthreads();
+    int bk[PER];
 #pragma unroll
-      for (int u = 0; u < U; ++u) {
-        const int q = p + u * G;
-        c[u] = q < p1 ? __ldg(col + q) : -1;
-        v[u] = q < p1 ? __ldg(vals + q) : 0.0;
+    for (int k = 0; k < PER; ++k) {
+      const int i = t + k * T;
+      bk[k] = -1;
+      if (i < rows) {
+        const int len = srp[i + 1] - srp[i];
+        const int b = min(len > 0 ? 32 - __clz(len) : 0, kRowBuckets - 1);
+        bk[k] = b;
+        atomicAdd(&cnt[b], 1);
       }
-      double xv[U];
-#pragma unroll
-      for (int u = 0; u < U; ++u) xv[u] = c[u] >= 0 ? __ldg(x + c[u]) : 0.0;
-#pragma unroll
-      for (int u = 0; u < U; ++u) s = fma(v[u], xv[u], s);
     }
-#pragma unroll
-    for (int o = G / 2; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-    if (i < n && sub == 0) {
-      if (bsub) s = bsub[i] - s;
-      y[i] = s;
-      nrm = fma(s, s, nrm);
+    __syncthreads();
+    if (t == 0) {
+      int o = 0, g = 0;
+      for (int b = 0; b < kRowBuckets; ++b) {
+        off[b] = o;
+        gst[b] = g;
+        const int per = 32 / bucket_lanes(b);
+        o += cnt[b];
+        g += (cnt[b] + per - 1) / per;
+      }
+      off[kRowBuckets] = o;
+      gst[kRowBuckets] = g;
     }
-    p0 = q0;
-    p1 = q1;
-    i = inext;
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < PER; ++k)
+      if (bk[k] >= 0) sorder[off[bk[k]] + atomicAdd(&fill[bk[k]], 1)] = static_cast<uint16_t>(t + k * T);
+    __syncthreads();
+    const int ngroups = gst[kRowBuckets];
+    for (int gi = warp; gi < ngroups; gi += T / 32) {
+      int b = 0;
+      while (b + 1 < kRowBuckets && gst[b + 1] <= gi) ++b;  // warp-uniform
+      const int G = bucket_lanes(b);
+      const int j = off[b] + (gi - gst[b]) * (32 / G) + lane / G;
+      const bool valid = j < off[b + 1];
+      const int r = valid ? sorder[j] : 0;
+      const int p0 = valid ? srp[r] : 0, p1 = valid ? srp[r + 1] : 0;
+      const int sub = lane & (G - 1);
+      double s;
+      switch (G) {
+        case 1: s = row_sum<1, U>(p0, p1, sub, col, vals, x); break;
+        case 2: s = row_sum<2, U>(p0, p1, sub, col, vals, x); break;
+        case 4: s = row_sum<4, U>(p0, p1, sub, col, vals, x); break;
+        case 8: s = row_sum<8, U>(p0, p1, sub, col, vals, x); break;
+        case 16: s = row_sum<16, U>(p0, p1, sub, col, vals, x); break;
+        default: s = row_sum<32, U>(p0, p1, sub, col, vals, x); break;
+      }
+      if (valid && sub == 0) {
+        if (bsub) s = bsub[r0 + r] - s;
+        y[r0 + r] = s;
+      }
+    }
+    __syncthreads();  // the segment's y is written (visible within the CTA)
+    for (int i = t; i < rows; i += T) {
+      const double v = y[r0 + i];
+      nrm = fma(v, v, nrm);
+    }
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) nrm += __shfl_xor_sync(0xffffffffu, nrm, o);
@@ -142,80 +217,6 @@ __global__ void __launch_bounds__(256) k_spmv_vec(int n, const int32_t* __restri
       if (lane == 0) norm_epilogue(epi, s, err);
     }
     if (t == 0) *counter = 0;
-  }
-}
-
-// ---- row order by length (for the lanes-per-row kernel) ----------------------------------------
-// A stable counting sort of the rows by the bucket floor(log2(len)) + 1 (capped at 11), in three
-// deterministic passes: counts per 256-row chunk, a per-bucket scan, and the scatter with ranks
-// from warp ballots. Rows that a warp then processes together have similar lengths, so a warp
-// does not iterate to the length of one long row while its other lanes idle.
-constexpr int kRowBuckets = 12;
-constexpr int kRowChunk = 256;
-
-__device__ __forceinline__ int row_bucket(const int32_t* row_ptr, int64_t i) {
-  const int len = row_ptr[i + 1] - row_ptr[i];
-  const int b = len > 0 ? 32 - __clz(len) : 0;
-  return b < kRowBuckets - 1 ? b : kRowBuckets - 1;
-}
-
-__global__ void __launch_bounds__(kRowChunk) k_row_count(int n, const int32_t* __restrict__ row_ptr,
-                                                         int32_t* __restrict__ counts) {
-  __shared__ int cnt[kRowBuckets];
-  const int t = threadIdx.x;
-  if (t < kRowBuckets) cnt[t] = 0;
-  __syncthreads();
-  const int64_t i = (int64_t)blockIdx.x * kRowChunk + t;
-  if (i < n) atomicAdd(&cnt[row_bucket(row_ptr, i)], 1);
-  __syncthreads();
-  if (t < kRowBuckets) counts[(int64_t)blockIdx.x * kRowBuckets + t] = cnt[t];
-}
-
-// One CTA, one warp per bucket: counts[c][b] becomes the position of chunk c's first row of
-// bucket b in the row order (buckets in increasing order, chunks in order within a bucket).
-__global__ void __launch_bounds__(32 * kRowBuckets) k_row_scan(int nchunks, int32_t* __restrict__ counts) {
-  __shared__ int total[kRowBuckets];
-  const int b = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  int carry = 0;
-  for (int c0 = 0; c0 < nchunks; c0 += 32) {
-    const int c = c0 + lane;
-    const int v = c < nchunks ? counts[(int64_t)c * kRowBuckets + b] : 0;
-    int incl = v;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const int u = __shfl_up_sync(0xffffffffu, incl, o);
-      if (lane >= o) incl += u;
-    }
-    if (c < nchunks) counts[(int64_t)c * kRowBuckets + b] = carry + incl - v;
-    carry += __shfl_sync(0xffffffffu, incl, 31);
-  }
-  if (lane == 0) total[b] = carry;
-  __syncthreads();
-  int base = 0;
-  for (int bb = 0; bb < b; ++bb) base += total[bb];
-  for (int c = lane; c < nchunks; c += 32) counts[(int64_t)c * kRowBuckets + b] += base;
-}
-
-__global__ void __launch_bounds__(kRowChunk) k_row_scatter(int n, const int32_t* __restrict__ row_ptr,
-                                                           const int32_t* __restrict__ offs,
-                                                           int32_t* __restrict__ perm) {
-  constexpr int W = kRowChunk / 32;
-  __shared__ int wcnt[W][kRowBuckets];
-  const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
-  const int64_t i = (int64_t)blockIdx.x * kRowChunk + t;
-  const bool valid = i < n;
-  const int b = valid ? row_bucket(row_ptr, i) : -1;
-  int rank = 0;
-  for (int bb = 0; bb < kRowBuckets; ++bb) {
-    const unsigned m = __ballot_sync(0xffffffffu, b == bb);
-    if (lane == 0) wcnt[warp][bb] = __popc(m);
-    if (b == bb) rank = __popc(m & ((1u << lane) - 1u));
-  }
-  __syncthreads();
-  if (valid) {
-    int before = 0;
-    for (int w = 0; w < warp; ++w) before += wcnt[w][b];
-    perm[offs[(int64_t)blockIdx.x * kRowBuckets + b] + before + rank] = static_cast<int32_t>(i);
   }
 }
 
@@ -307,20 +308,8 @@ int spmv_lanes_per_row(int n, int64_t nnz) {
   return mean < 12.0 ? 1 : 4;
 }
 
-size_t row_order_scratch_bytes(int n) { return (size_t)((n + kRowChunk - 1) / kRowChunk) * kRowBuckets * 4; }
-
-int launch_row_order(int n, const int32_t* row_ptr, int32_t* perm, int32_t* scratch, cudaStream_t stream) {
-  if (n <= 0) return CBG_OK;
-  const int nchunks = (n + kRowChunk - 1) / kRowChunk;
-  k_row_count<<<nchunks, kRowChunk, 0, stream>>>(n, row_ptr, scratch);
-  k_row_scan<<<1, 32 * kRowBuckets, 0, stream>>>(nchunks, scratch);
-  k_row_scatter<<<nchunks, kRowChunk, 0, stream>>>(n, row_ptr, scratch, perm);
-  cudaError_t e = cudaGetLastError();
-  return e == cudaSuccess ? CBG_OK : cuda_fail(e, "row order launch");
-}
-
 int launch_spmv(int n, int64_t nnz, const int32_t* row_ptr, const int32_t* col, const double* vals, const double* x,
-                double* y, const double* bsub, const int32_t* perm, double* partials, unsigned int* counter, int* err,
+                double* y, const double* bsub, double* partials, unsigned int* counter, int* err,
                 const NormEpilogue& epi, const Gate& gate, cudaStream_t stream) {
   if (n <= 0) return CBG_OK;
   const int g = spmv_lanes_per_row(n, nnz);
@@ -328,9 +317,10 @@ int launch_spmv(int n, int64_t nnz, const int32_t* row_ptr, const int32_t* col, 
     const int grid = grid_rows(n, 8);
     k_spmv<<<grid, 256, 0, stream>>>(n, row_ptr, col, vals, x, y, bsub, partials, counter, err, epi, gate);
   } else {
-    const int grid = grid_rows((int64_t)n * g, 8);
-    k_spmv_vec<4, 8><<<grid, 256, 0, stream>>>(n, row_ptr, col, vals, x, y, bsub, perm, partials, counter, err, epi,
-                                               gate);
+    // one segment of kSeg rows per CTA and turn; as many CTAs as the GPU holds
+    const int grid = grid_rows(((int64_t)n + kSeg - 1) / kSeg * 256, CBG_SPMV_CTAS_PER_SM);
+    k_spmv_seg<CBG_SPMV_LOADS><<<grid, 256, 0, stream>>>(n, row_ptr, col, vals, x, y, bsub, partials, counter, err,
+                                                         epi, gate);
   }
   cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? CBG_OK : cuda_fail(e, "spmv launch");

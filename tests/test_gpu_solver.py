@@ -50,6 +50,30 @@ def test_spmv(cbg, orc, matrix):
     assert cbg.csr_validate(Ad.row_ptr, Ad.col) == 0
 
 
+@pytest.mark.parametrize("n", [37, 5000])
+def test_spmv_every_length_bucket(cbg, orc, n):
+    """Long rows take a row order sorted by length bucket with 1 to 32 lanes per row by bucket:
+    rows of every length from 0 (empty) to 3 000 entries, in a random order, mean above 12, against
+    the oracle; the fused norm too, and the residual form b - A x through a solve's first step."""
+    rng = np.random.default_rng(n)
+    lens = rng.choice([0, 1, 2, 3, 5, 9, 17, 33, 70, 140, 300, 700, 1500, 3000], size=n)
+    lens = np.minimum(lens, n)
+    rp = np.zeros(n + 1, dtype=np.int64)
+    rp[1:] = np.cumsum(lens)
+    col = np.concatenate([np.sort(rng.choice(n, size=k, replace=False)) for k in lens]).astype(np.int32)
+    vals = rng.standard_normal(col.size)
+    rp = rp.astype(np.int32)
+    assert col.size / n >= 12 and (lens == 0).any()
+    x = rng.standard_normal(n)
+    Rp, Col, Vals = (torch.from_numpy(a).cuda() for a in (rp, col, vals))
+    nrm = torch.zeros(1, dtype=torch.float64, device="cuda")
+    y = cbg.spmv(Rp, Col, Vals, torch.from_numpy(x).cuda(), norm2=nrm).cpu().numpy()
+    ref = orc.spmv(rp, col, vals, x)
+    absum = np.array([np.abs(vals[rp[i]:rp[i + 1]] * x[col[rp[i]:rp[i + 1]]]).sum() for i in range(n)])
+    assert np.all(np.abs(y - ref) <= 2 * np.maximum(lens, 1) * 2.0 ** -53 * absum + 1e-300)
+    assert abs(nrm.item() - orc.dot2(y, y)) <= 1e-12 * orc.dot2(y, y)
+
+
 def test_bad_matrix_rejected(cbg):
     A, _ = c1()
     Ad = A.to("cuda")
