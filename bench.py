@@ -57,6 +57,15 @@ def stored_bytes(fmt: str, l: int, n: int) -> int:
     return n * VALUE_BYTES[fmt]
 
 
+def step_config(args, workload: str, world: int) -> dict:
+    """The bench line's config: the same dict on the GPU arm and the reference arm (the oracle), so
+    both lines name one workload."""
+    per_step = sum(step_bytes(args.fmt, args.bits, args.n, args.nvec).values())
+    return {"workload": workload, "n": args.n, "nvec": args.nvec, "format": args.fmt, "frsz2_bits": args.bits,
+            "bytes_per_step": per_step, "l2": "inputs larger than L2 (no flush needed)",
+            "parallelism": f"replicas x{world}" if world > 1 else "1 GPU"}
+
+
 def step_bytes(fmt: str, l: int, n: int, nvec: int):
     vb = stored_bytes(fmt, l, n)
     return {"store": 8 * n + vb, "dot": nvec * vb + 8 * n, "update": nvec * vb + 16 * n}
@@ -769,7 +778,7 @@ def main():
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3 / args.steps,
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
                 "data": "synthetic",
-                "config": {"workload": workload, "n": args.n, "nvec": args.nvec, "oracle_sample_n": n},
+                "config": step_config(args, workload, world),
                 "cpu_baseline": {"value": gbs, "unit": "GB/s", "cores": cores, "kind": "oracle",
                                  "sample": f"each step over {args.nvec} x {n} values of the workload, rows split "
                                            f"over {cores} threads"},
@@ -865,9 +874,7 @@ def main():
     line = {"metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": workload, "n": args.n, "nvec": args.nvec, "format": fmt, "frsz2_bits": l,
-                       "bytes_per_step": per_step, "l2": "inputs larger than L2 (no flush needed)",
-                       "parallelism": f"replicas x{world}" if world > 1 else "1 GPU"},
+            "config": step_config(args, workload, world),
             "roofline": roofline, "gpu_launches": 3 * args.steps, "clocks": clocks}
 
     if e2e:

@@ -34,6 +34,14 @@ def test_reference_arm_line():
     cb = line["cpu_baseline"]
     assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == line["value"] and cb["sample"]
     assert line["e2e"] == {"value": line["value"], "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
+    # the same config dict as the GPU arm's line for the same arguments (one workload, one config)
+    sys.path.insert(0, ROOT)
+    import argparse
+
+    import bench
+
+    args = argparse.Namespace(fmt="frsz2", bits=32, n=65536, nvec=4)
+    assert line["config"] == bench.step_config(args, line["config"]["workload"], 1)
 
 
 def test_reference_arm_other_ranks_exit_quietly():
