@@ -10,13 +10,14 @@
 // few.
 //
 // Matrices with long rows (mean >= 12 nonzeros, e.g. power-law row lengths): a CTA takes 512
-// consecutive rows, sorts them in shared memory by length bucket (floor(log2 len) + 1) and gives
-// each bucket its own number G of lanes per row, about 8-16 nonzeros per lane. A warp then serves
-// 32/G rows of lengths within a factor of two, so few lanes idle while it iterates to its longest
-// row (GB300 issues every FP64 warp instruction at full cost, whatever its active lanes), the row
-// sum costs log2(G) shuffle-adds, and the rows of a segment are read close together in time, so the
-// sectors that neighbouring rows share come from DRAM once (a global sort by length scattered them:
-// 1.47x the algorithmic DRAM bytes).
+// consecutive rows and sorts them in shared memory by a length key (the exact length below 64,
+// eighths of an octave above), longest first. Each length class gets its own number G of lanes per
+// row, 8-16 nonzeros per lane, so a warp serves 32/G rows of nearly equal length. GB300 issues an
+// FP64 warp instruction at full cost whatever its active lanes, and the SpMV's FP64 time is close
+// to its HBM time, so the warp issues exactly as many FMAs as its longest lane needs (no chunk
+// padding). The row sum costs log2(G) shuffle-adds; the rows of a segment are read close together
+// in time, so the sectors that neighbouring rows share come from DRAM once (a global sort by
+// length scattered them: 1.47x the algorithmic DRAM bytes).
 #include "common.cuh"
 #include "kernels.cuh"
 
@@ -76,47 +77,93 @@ __global__ void __launch_bounds__(256) k_spmv(int n, const int32_t* __restrict__
 #ifndef CBG_SPMV_CTAS_PER_SM
 #define CBG_SPMV_CTAS_PER_SM 8
 #endif
-constexpr int kRowBuckets = 12;  // floor(log2 len) + 1, capped: bucket 0 holds the empty rows
-constexpr int kSeg = 512;        // rows a CTA sorts and serves at a time
+constexpr int kSeg = 512;                     // rows a CTA sorts and serves at a time
+constexpr int kExactKeys = 64;                // rows shorter than this are keyed by their exact length
+constexpr int kLenKeys = kExactKeys + 5 * 8;  // then 8 keys per octave up to 2047, the last one capped
+constexpr int kLaneClasses = 6;               // G = 32, 16, 8, 4, 2, 1 lanes per row
+// the sort keys of lane class c (G = 32 >> c) are [kClassLo[c], kClassLo[c - 1]), kClassLo[-1] = kLenKeys
+__constant__ int kClassLo[kLaneClasses] = {kExactKeys + 16, kExactKeys + 8, kExactKeys, 32, 16, 0};
 
-// Lanes per row for rows of bucket b (lengths [2^(b-1), 2^b)): about 8-16 nonzeros per lane, at
-// most a warp per row.
-__device__ __forceinline__ int bucket_lanes(int b) {
-  const int g = b >= 5 ? 1 << (b - 4) : 1;
-  return g < 32 ? g : 32;
+// Sort key of a row of `len` nonzeros: the length itself below 64, else its octave and the three
+// bits after the leading one (lengths within 12.5% share a key); 2048 and more share the top key.
+// Keys ascend with the length, and each lane class is a contiguous range of keys: G = 1 below 16
+// nonzeros, 2 below 32, 4 below 64, 8 below 128, 16 below 256, else 32 (8-16 nonzeros per lane).
+__device__ __forceinline__ int len_key(int len) {
+  if (len < kExactKeys) return len;
+  const int b = 31 - __clz(len);
+  if (b >= 11) return kLenKeys - 1;
+  return kExactKeys + (b - 6) * 8 + ((len >> (b - 3)) & 7);
 }
 
-// The sum of a row over G consecutive lanes (sub = lane % G): each lane keeps U independent
-// (column, value, x-gather) loads in flight before its FMAs, one FMA chain per lane, and the G lanes
-// combine in a fixed shuffle order (deterministic).
+// s + v[0] x[0] + ... + v[K-1] x[K-1], one FMA chain.
+template <int K>
+__device__ __forceinline__ double fma_chain(const double* v, const double* xv, double s) {
+#pragma unroll
+  for (int u = 0; u < K; ++u) s = fma(v[u], xv[u], s);
+  return s;
+}
+
+// U (column, value) loads of one lane from p, p + G, ... (positions past p1 give 0), then the U
+// x-gathers: all in flight before the FMAs.
+template <int G, int U>
+__device__ __forceinline__ void row_chunk(int p, int p1, const int32_t* __restrict__ col,
+                                          const double* __restrict__ vals, const double* __restrict__ x, double* v,
+                                          double* xv) {
+  int c[U];
+#pragma unroll
+  for (int u = 0; u < U; ++u) {
+    const int q = p + u * G;
+    c[u] = q < p1 ? __ldg(col + q) : -1;
+    v[u] = q < p1 ? __ldg(vals + q) : 0.0;
+  }
+#pragma unroll
+  for (int u = 0; u < U; ++u) xv[u] = c[u] >= 0 ? __ldg(x + c[u]) : 0.0;
+}
+
+// The sum of a row over G consecutive lanes (sub = lane % G), lane sub taking nonzeros p0 + sub,
+// p0 + sub + G, ... in order, one FMA chain per lane; the G lanes then combine in a fixed shuffle
+// order (deterministic). The whole warp runs to the largest per-lane count of its rows, mw, in
+// chunks of U loads and then one chunk of exactly mw mod U FMAs, so the warp issues mw FMAs: GB300
+// issues an FP64 warp instruction at full cost whatever its active lanes, so no FMA is padded to a
+// chunk boundary, and the rows of a warp have nearly equal lengths (sorted by key).
 template <int G, int U>
 __device__ __forceinline__ double row_sum(int p0, int p1, int sub, const int32_t* __restrict__ col,
                                           const double* __restrict__ vals, const double* __restrict__ x) {
+  static_assert(U == 4 || U == 8, "the tail switch covers chunks of 4 or 8 loads");
+  const int len = p1 - p0;
+  const int m = len > sub ? (len - sub + G - 1) / G : 0;
+  const int mw = static_cast<int>(__reduce_max_sync(0xffffffffu, static_cast<unsigned>(m)));
   double s = 0.0;
-  for (int p = p0 + sub; p < p1; p += G * U) {
-    int c[U];
-    double v[U];
-#pragma unroll
-    for (int u = 0; u < U; ++u) {
-      const int q = p + u * G;
-      c[u] = q < p1 ? __ldg(col + q) : -1;
-      v[u] = q < p1 ? __ldg(vals + q) : 0.0;
+  double v[U], xv[U];
+  int p = p0 + sub;
+  for (int k = mw / U; k > 0; --k, p += G * U) {
+    row_chunk<G, U>(p, p1, col, vals, x, v, xv);
+    s = fma_chain<U>(v, xv, s);
+  }
+  const int rem = mw % U;  // warp-uniform
+  if (rem > 0) {
+    row_chunk<G, U>(p, p1, col, vals, x, v, xv);
+    switch (rem) {
+      case 1: s = fma_chain<1>(v, xv, s); break;
+      case 2: s = fma_chain<2>(v, xv, s); break;
+      case 3: s = fma_chain<3>(v, xv, s); break;
+      case 4: s = fma_chain<(U > 4 ? 4 : 1)>(v, xv, s); break;
+      case 5: s = fma_chain<(U > 5 ? 5 : 1)>(v, xv, s); break;
+      case 6: s = fma_chain<(U > 6 ? 6 : 1)>(v, xv, s); break;
+      default: s = fma_chain<(U > 7 ? 7 : 1)>(v, xv, s); break;
     }
-    double xv[U];
-#pragma unroll
-    for (int u = 0; u < U; ++u) xv[u] = c[u] >= 0 ? __ldg(x + c[u]) : 0.0;
-#pragma unroll
-    for (int u = 0; u < U; ++u) s = fma(v[u], xv[u], s);
   }
 #pragma unroll
   for (int o = G / 2; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
   return s;
 }
 
-// A CTA serves segments of kSeg rows (grid-strided): the segment's row pointers go to shared
-// memory, its rows are ordered by bucket there (within a bucket in any order: each row's sum does
-// not depend on it), and warps take work groups of 32/G rows of one bucket in turn. ||y||^2 is
-// then summed over the segment in row order, so it is deterministic.
+// A CTA serves segments of kSeg rows (grid-strided). The segment's row pointers go to shared
+// memory; a counting sort on the length key orders its rows from the longest down; warps then take
+// work groups of 32/G rows of one lane class from a shared counter, the longest rows first, so that
+// the warps reach the segment's end together. The order within a key is arbitrary: each row's sum
+// depends only on the row and its key. ||y||^2 is then summed over the segment in row order, so it
+// is deterministic.
 template <int U>
 __global__ void __launch_bounds__(256) k_spmv_seg(int n, const int32_t* __restrict__ row_ptr,
                                                   const int32_t* __restrict__ col, const double* __restrict__ vals,
@@ -126,70 +173,94 @@ __global__ void __launch_bounds__(256) k_spmv_seg(int n, const int32_t* __restri
   if (gate_skip_s(gate)) return;
   __shared__ int srp[kSeg + 1];
   __shared__ uint16_t sorder[kSeg];
-  __shared__ int cnt[kRowBuckets], fill[kRowBuckets], off[kRowBuckets + 1], gst[kRowBuckets + 1];
+  __shared__ int cnt[kLenKeys], off[kLenKeys];
+  __shared__ int cls[kLaneClasses + 1], grp[kLaneClasses + 1];
+  __shared__ int next;
   __shared__ double red[8];
   __shared__ int flag;
   constexpr int T = 256, PER = kSeg / T;
+  static_assert(kLenKeys <= 4 * 32, "one warp scans the keys, four per lane");
   const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
   double nrm = 0.0;
   const int nseg = (n + kSeg - 1) / kSeg;
   for (int sg = blockIdx.x; sg < nseg; sg += gridDim.x) {
     const int r0 = sg * kSeg, rows = min(kSeg, n - r0);
     __syncthreads();  // the previous segment's shared arrays are no longer read
-    if (t < kRowBuckets) {
-      cnt[t] = 0;
-      fill[t] = 0;
-    }
+    for (int i = t; i < kLenKeys; i += T) cnt[i] = 0;
+    if (t == 0) next = 0;
     for (int i = t; i <= rows; i += T) srp[i] = __ldg(row_ptr + r0 + i);
     __syncthreads();
-    int bk[PER];
+    int key[PER];
 #pragma unroll
     for (int k = 0; k < PER; ++k) {
       const int i = t + k * T;
-      bk[k] = -1;
-      if (i < rows) {
-        const int len = srp[i + 1] - srp[i];
-        const int b = min(len > 0 ? 32 - __clz(len) : 0, kRowBuckets - 1);
-        bk[k] = b;
-        atomicAdd(&cnt[b], 1);
-      }
+      key[k] = i < rows ? len_key(srp[i + 1] - srp[i]) : -1;
+      if (key[k] >= 0) atomicAdd(&cnt[key[k]], 1);
     }
     __syncthreads();
-    if (t == 0) {
-      int o = 0, g = 0;
-      for (int b = 0; b < kRowBuckets; ++b) {
-        off[b] = o;
-        gst[b] = g;
-        const int per = 32 / bucket_lanes(b);
-        o += cnt[b];
-        g += (cnt[b] + per - 1) / per;
+    if (warp == 0) {
+      // off[key] := rows with a larger key (descending order), lane l holding positions 4l .. 4l+3
+      int c4[4], s = 0;
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const int kk = kLenKeys - 1 - (4 * lane + j);
+        c4[j] = kk >= 0 ? cnt[kk] : 0;
+        s += c4[j];
       }
-      off[kRowBuckets] = o;
-      gst[kRowBuckets] = g;
+      int incl = s;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int u = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += u;
+      }
+      int run = incl - s;
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const int kk = kLenKeys - 1 - (4 * lane + j);
+        if (kk >= 0) off[kk] = run;
+        run += c4[j];
+      }
+      __syncwarp();
+      if (lane == 0) {
+        // class c's rows are [cls[c], cls[c + 1]) of the sorted order, its work groups start at grp[c]
+        int g = 0;
+        for (int c = 0; c < kLaneClasses; ++c) {
+          cls[c] = off[(c == 0 ? kLenKeys : kClassLo[c - 1]) - 1];
+          grp[c] = g;
+          const int end = off[kClassLo[c]] + cnt[kClassLo[c]];
+          g += (end - cls[c] + (1 << c) - 1) >> c;  // 32 / G = 2^c rows per group
+        }
+        cls[kLaneClasses] = rows;
+        grp[kLaneClasses] = g;
+      }
     }
     __syncthreads();
 #pragma unroll
     for (int k = 0; k < PER; ++k)
-      if (bk[k] >= 0) sorder[off[bk[k]] + atomicAdd(&fill[bk[k]], 1)] = static_cast<uint16_t>(t + k * T);
+      if (key[k] >= 0) sorder[atomicAdd(&off[key[k]], 1)] = static_cast<uint16_t>(t + k * T);
     __syncthreads();
-    const int ngroups = gst[kRowBuckets];
-    for (int gi = warp; gi < ngroups; gi += T / 32) {
-      int b = 0;
-      while (b + 1 < kRowBuckets && gst[b + 1] <= gi) ++b;  // warp-uniform
-      const int G = bucket_lanes(b);
-      const int j = off[b] + (gi - gst[b]) * (32 / G) + lane / G;
-      const bool valid = j < off[b + 1];
+    const int ngroups = grp[kLaneClasses];
+    for (;;) {
+      int gi = 0;
+      if (lane == 0) gi = atomicAdd(&next, 1);
+      gi = __shfl_sync(0xffffffffu, gi, 0);
+      if (gi >= ngroups) break;
+      int c = 0;
+      while (grp[c + 1] <= gi) ++c;  // warp-uniform; gi < grp[kLaneClasses]
+      const int G = 32 >> c;
+      const int j = cls[c] + ((gi - grp[c]) << c) + (lane >> (5 - c));
+      const bool valid = j < cls[c + 1];
       const int r = valid ? sorder[j] : 0;
       const int p0 = valid ? srp[r] : 0, p1 = valid ? srp[r + 1] : 0;
       const int sub = lane & (G - 1);
       double s;
-      switch (G) {
-        case 1: s = row_sum<1, U>(p0, p1, sub, col, vals, x); break;
-        case 2: s = row_sum<2, U>(p0, p1, sub, col, vals, x); break;
-        case 4: s = row_sum<4, U>(p0, p1, sub, col, vals, x); break;
-        case 8: s = row_sum<8, U>(p0, p1, sub, col, vals, x); break;
-        case 16: s = row_sum<16, U>(p0, p1, sub, col, vals, x); break;
-        default: s = row_sum<32, U>(p0, p1, sub, col, vals, x); break;
+      switch (c) {
+        case 0: s = row_sum<32, U>(p0, p1, sub, col, vals, x); break;
+        case 1: s = row_sum<16, U>(p0, p1, sub, col, vals, x); break;
+        case 2: s = row_sum<8, U>(p0, p1, sub, col, vals, x); break;
+        case 3: s = row_sum<4, U>(p0, p1, sub, col, vals, x); break;
+        case 4: s = row_sum<2, U>(p0, p1, sub, col, vals, x); break;
+        default: s = row_sum<1, U>(p0, p1, sub, col, vals, x); break;
       }
       if (valid && sub == 0) {
         if (bsub) s = bsub[r0 + r] - s;

@@ -52,11 +52,18 @@ def test_spmv(cbg, orc, matrix):
 
 @pytest.mark.parametrize("n", [37, 5000])
 def test_spmv_every_length_bucket(cbg, orc, n):
-    """Long rows take a row order sorted by length bucket with 1 to 32 lanes per row by bucket:
-    rows of every length from 0 (empty) to 3 000 entries, in a random order, mean above 12, against
-    the oracle; the fused norm too, and the residual form b - A x through a solve's first step."""
+    """Long rows (mean length 12 or more) are sorted within 512-row segments by a length key (the
+    exact length below 64, eighths of an octave above, one key for 2048 and more) and get 1 to 32
+    lanes per row by length. Rows of every length from 0 (empty) to 80, and log-uniform lengths up
+    to 3 000, in a random order, against the oracle: every exact key, every per-lane count modulo
+    the load chunk, and every lane class; the fused norm too. (The residual form b - A x runs in the
+    power-law solves of this file.)"""
     rng = np.random.default_rng(n)
-    lens = rng.choice([0, 1, 2, 3, 5, 9, 17, 33, 70, 140, 300, 700, 1500, 3000], size=n)
+    short = rng.integers(0, 81, size=n)
+    long_ = np.exp(rng.uniform(np.log(81), np.log(3000), size=n)).astype(np.int64)
+    lens = np.where(rng.random(n) < 0.6, short, long_)
+    lens[:min(n, 81)] = np.arange(min(n, 81))
+    lens = rng.permutation(lens)
     lens = np.minimum(lens, n)
     rp = np.zeros(n + 1, dtype=np.int64)
     rp[1:] = np.cumsum(lens)
@@ -73,6 +80,23 @@ def test_spmv_every_length_bucket(cbg, orc, n):
     assert np.all(np.abs(y - ref) <= 2 * np.maximum(lens, 1) * 2.0 ** -53 * absum + 1e-300)
     assert abs(nrm.item() - orc.dot2(y, y)) <= 1e-12 * orc.dot2(y, y)
 
+
+
+def test_spmv_powerlaw_several_segments_per_cta(cbg, orc):
+    """The long-row kernel on a power-law matrix of 700 000 rows (the C4 generator: Pareto lengths
+    10-2000, mean 29): 1 368 segments, more than the grid's CTAs, so CTAs serve several segments in
+    turn and the norm partials sum over them; against the oracle, element by element."""
+    A = workloads.powerlaw(700_000, seed=5)
+    rp, col, vals = A.numpy()
+    x = workloads.uniform_vector(A.n, 9).numpy()
+    Ad = A.to("cuda")
+    nrm = torch.zeros(1, dtype=torch.float64, device="cuda")
+    y = cbg.spmv(Ad.row_ptr, Ad.col, Ad.vals, torch.from_numpy(x).cuda(), norm2=nrm).cpu().numpy()
+    ref = orc.spmv(rp, col, vals, x)
+    lens = np.diff(rp)
+    absum = np.bincount(np.repeat(np.arange(A.n), lens), weights=np.abs(vals * x[col]), minlength=A.n)
+    assert np.all(np.abs(y - ref) <= 2 * np.maximum(lens, 1) * 2.0 ** -53 * absum + 1e-300)
+    assert abs(nrm.item() - orc.dot2(y, y)) <= 1e-12 * orc.dot2(y, y)
 
 def test_bad_matrix_rejected(cbg):
     A, _ = c1()
