@@ -52,6 +52,42 @@ __device__ __forceinline__ long long round_shift_right(long long x, int d) {
   return (x + (1ll << (d - 1))) >> d;
 }
 
+// A finite double as th * 2^xb exactly (th carries the significand, at most 53 bits, and the sign).
+__device__ __forceinline__ void split_double(double v, long long& th, int& xb) {
+  const uint64_t u = static_cast<uint64_t>(__double_as_longlong(v));
+  const int e = static_cast<int>((u >> 52) & 0x7FF);
+  long long m = static_cast<long long>(u & ((1ull << 52) - 1));
+  if (e) m |= 1ll << 52;
+  th = (u >> 63) ? -m : m;
+  xb = (e ? e : 1) - 1075;
+}
+
+// The sum over a warp of its lanes' th * 2^xb (|th| < 2^62), returned as S * 2^X on every lane.
+// 2^M bounds the warp's largest term and X = M - 57: each term is rounded once to 2^X units
+// (nearest, ties up; an error below 2^-58 of the largest term), and the rounded terms, each at most
+// 2^57 in magnitude, add up exactly: three 21-bit slices summed by integer warp reductions, so
+// the sum of the 32 terms needs no floating point at all.
+__device__ __forceinline__ long long warp_fixed_sum(long long th, int xb, int& X) {
+  const unsigned long long A = static_cast<unsigned long long>(th < 0 ? -th : th);
+  const int mag = A ? xb + 64 - __clzll(static_cast<long long>(A)) : -(1 << 30);
+  const int M = __reduce_max_sync(0xffffffffu, mag);
+  X = M - 57;
+  long long q = 0;
+  if (A) {
+    const int d = X - xb;
+    if (d <= 0)
+      q = static_cast<long long>(static_cast<unsigned long long>(th) << (-d));  // -d <= 57 - bitlength
+    else if (d < 63)
+      q = (th + (1ll << (d - 1))) >> d;  // |th| < 2^62: no overflow
+  }
+  const int lo = static_cast<int>(q & 0x1FFFFF), mid = static_cast<int>((q >> 21) & 0x1FFFFF);
+  const int hi = static_cast<int>(q >> 42);  // |hi| <= 2^15
+  const long long slo = __reduce_add_sync(0xffffffffu, lo);    // < 2^26
+  const long long smid = __reduce_add_sync(0xffffffffu, mid);  // < 2^26
+  const long long shi = __reduce_add_sync(0xffffffffu, hi);    // |.| <= 2^20
+  return shi * (1ll << 42) + smid * (1ll << 21) + slo;
+}
+
 // Prefetch `bytes` (multiple of 16, 16-byte aligned) of global memory into L2 with the bulk-copy unit.
 __device__ __forceinline__ void bulk_prefetch_l2(const void* p, uint32_t bytes) {
   asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");

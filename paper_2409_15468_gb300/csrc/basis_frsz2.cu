@@ -76,15 +76,11 @@ struct FDot {
   static constexpr int kWarps = kThreads / 32;
   static constexpr int kVps = L == 16 ? CBG_DOT_VPS_16 : (L == 21 ? CBG_DOT_VPS_21 : CBG_DOT_VPS_32);
   static constexpr int kStages = L == 16 ? CBG_DOT_STAGES_16 : (L == 21 ? CBG_DOT_STAGES_21 : CBG_DOT_STAGES_32);
-  static constexpr int kBatch = 4;       // vectors per per-warp reduction
-  static constexpr int kRedStride = 33;  // doubles per batch row (padded against bank conflicts)
   static constexpr int kCodeBytes = kThreads * L * 4;
   static constexpr int kVecBytes = kCodeBytes + (H ? 0 : kThreads * 4);  // one vector's codes and exponents
   static constexpr int kStageBytes = kVps * kVecBytes;
-  static constexpr int kRedDoubles = kWarps * kBatch * kRedStride;
   static size_t smem_bytes(int nvec) {
-    return (size_t)kStages * kStageBytes + (size_t)kRedDoubles * 8 + (size_t)kWarps * nvec * 8 +
-           2 * kStages * 8 + 16;
+    return (size_t)kStages * kStageBytes + (size_t)kWarps * nvec * 8 + 2 * kStages * 8 + 16;
   }
 };
 
@@ -98,8 +94,7 @@ __device__ __forceinline__ void dot_body(const BasisView& B, int nvec, const dou
   if (gate_skip(gate)) return;
   extern __shared__ __align__(128) uint8_t smem[];
   uint8_t* stages = smem;
-  double* red = reinterpret_cast<double*>(smem + S * C::kStageBytes);
-  double* hpart = red + C::kRedDoubles;
+  double* hpart = reinterpret_cast<double*>(smem + S * C::kStageBytes);
   uint64_t* full = reinterpret_cast<uint64_t*>(hpart + C::kWarps * nvec);
   uint64_t* empty = full + S;
   int* flags = reinterpret_cast<int*>(empty + S);  // [0] abort, [1] last-CTA flag
@@ -151,8 +146,9 @@ __device__ __forceinline__ void dot_body(const BasisView& B, int nvec, const dou
     for (; issued < S && issued < total; ++issued) issue(issued);
   }
 
-  double* myred = red + warp * C::kBatch * C::kRedStride;
   double* myh = hpart + warp * nvec;
+  long long ks = 0;  // lane i: the warp's sum for vector 32 k + i of the current batch, ks * 2^kx
+  int kx = 0;
   int s = 0;           // stage of the current vector and the phase parity of its barriers
   uint32_t ph = 0;
   int ps = 0;          // stage and parity of the previous vector (refilled by thread 0)
@@ -228,7 +224,8 @@ __device__ __forceinline__ void dot_body(const BasisView& B, int nvec, const dou
       for (int j = 0; j < VPS; ++j) {
         const int vj = vi + j;
         if (vj >= nv) break;  // uniform
-        double hp = 0.0;
+        long long th = 0;  // this block's sum: th * 2^xb
+        int xb = 0;
         if (active && ok) {
           const uint8_t* st = stages + s * C::kStageBytes + j * C::kVecBytes;
           const uint32_t* cw = reinterpret_cast<const uint32_t*>(st) + t * L;
@@ -240,9 +237,8 @@ __device__ __forceinline__ void dot_body(const BasisView& B, int nvec, const dou
             // Rounded to 2^(l-5) units it fits in 63 bits; the rounding error, at most 2^(l-6)
             // units, is a quarter of the bound 2^-54 max|w| sum|vhat| of a block whose maxima are
             // normal.
-            const long long th = (a1 << (32 - L)) + ((a0 + (1ll << (L - 6))) >> (L - 5));
-            const int x = (e > 1 ? static_cast<int>(e) : 1) + ew - 2096 - L;
-            hp = scale_pow2(static_cast<double>(th), x + L - 5);
+            th = (a1 << (32 - L)) + ((a0 + (1ll << (L - 6))) >> (L - 5));
+            xb = (e > 1 ? static_cast<int>(e) : 1) + ew - 2101;
           } else {
             uint32_t emax = 0;
             block_dot_fp16(cw, t, W1, W0, a1, a0, emax);
@@ -253,11 +249,11 @@ __device__ __forceinline__ void dot_body(const BasisView& B, int nvec, const dou
               const unsigned long long A = static_cast<unsigned long long>(a1 < 0 ? -a1 : a1);
               const int bl = 64 - __clzll(static_cast<long long>(A));
               const int u = bl > 35 ? bl - 35 : 0;
-              const long long th = u == 0 ? (a1 << 27) + a0 : (a1 << (27 - u)) + ((a0 + (1ll << (u - 1))) >> u);
-              hp = scale_pow2(static_cast<double>(th), u + ew - 1099);
+              th = u == 0 ? (a1 << 27) + a0 : (a1 << (27 - u)) + ((a0 + (1ll << (u - 1))) >> u);
+              xb = u + ew - 1099;
             } else {
               // a value of magnitude >= 2 in the block (not a Krylov vector): the FP64 dot of the
-              // decoded values with w, read again from memory
+              // decoded values with w, read again from memory, taken exactly as th * 2^xb
               const uint16_t* hv = reinterpret_cast<const uint16_t*>(cw);
               const double* wb = w + b * 32;
               const int64_t rem = B.n - b * 32;
@@ -265,27 +261,24 @@ __device__ __forceinline__ void dot_body(const BasisView& B, int nvec, const dou
 #pragma unroll 1
               for (int k = 0; k < 32; ++k)
                 if (k < rem) acc = fma(widen_f16(hv[k]), __ldg(wb + k), acc);
-              hp = acc;
+              split_double(acc, th, xb);
             }
           }
         }
-        myred[(vj % C::kBatch) * C::kRedStride + lane] = hp;
-        if (vj % C::kBatch == C::kBatch - 1 || vj == nv - 1) {
-          // row r of the batch holds vector first_v + r; lane (v, part) sums kBatch entries of
-          // row v, then the parts combine with shuffles
-          constexpr int KB = C::kBatch;
-          __syncwarp();
-          const int first_i = vj - (vj % KB), cnt = vj - first_i + 1, first_v = v_lo + first_i;
-          const int v = lane % KB, part = lane / KB;
-          double sacc = 0.0;
-          if (v < cnt) {
-#pragma unroll
-            for (int i = 0; i < KB; ++i) sacc += myred[v * C::kRedStride + part * KB + i];
+        // the warp's 32 block sums at a common scale, exactly in integers; lane vj % 32 keeps vector
+        // vj's, and every 32 vectors each lane converts its vector once and adds it to the warp's
+        // per-vector sum (one FP64 instruction per 32 vectors)
+        int X;
+        const long long sum = warp_fixed_sum(th, xb, X);
+        if (lane == (vj & 31)) {
+          ks = sum;
+          kx = X;
+        }
+        if ((vj & 31) == 31 || vj == nv - 1) {
+          if (lane <= (vj & 31)) {
+            double* hv = myh + v_lo + (vj & ~31) + lane;
+            *hv = fma_pow2(static_cast<double>(ks), kx, *hv);
           }
-#pragma unroll
-          for (int o = KB; o < 32; o <<= 1) sacc += __shfl_xor_sync(0xffffffffu, sacc, o);
-          if (part == 0 && v < cnt) myh[first_v + v] += sacc;
-          __syncwarp();
         }
       }
       __syncwarp();

@@ -121,8 +121,9 @@ __device__ __forceinline__ void row_chunk(int p, int p1, const int32_t* __restri
 }
 
 // The sum of a row over G consecutive lanes (sub = lane % G), lane sub taking nonzeros p0 + sub,
-// p0 + sub + G, ... in order, one FMA chain per lane; the G lanes then combine in a fixed shuffle
-// order (deterministic). The whole warp runs to the largest per-lane count of its rows, mw, in
+// p0 + sub + G, ... in order: the full chunks into two FMA chains (even and odd chunk positions),
+// added together before the last partial chunk; the G lanes then combine in a fixed shuffle order
+// (deterministic). The whole warp runs to the largest per-lane count of its rows, mw, in
 // chunks of U loads and then one chunk of exactly mw mod U FMAs, so the warp issues mw FMAs: GB300
 // issues an FP64 warp instruction at full cost whatever its active lanes, so no FMA is padded to a
 // chunk boundary, and the rows of a warp have nearly equal lengths (sorted by key).
@@ -136,10 +137,16 @@ __device__ __forceinline__ double row_sum(int p0, int p1, int sub, const int32_t
   double s = 0.0;
   double v[U], xv[U];
   int p = p0 + sub;
+  double s2 = 0.0;  // GB300's dependent FP64 latency is ~64 cycles: two chains halve the wait
   for (int k = mw / U; k > 0; --k, p += G * U) {
     row_chunk<G, U>(p, p1, col, vals, x, v, xv);
-    s = fma_chain<U>(v, xv, s);
+#pragma unroll
+    for (int u = 0; u < U; u += 2) {
+      s = fma(v[u], xv[u], s);
+      s2 = fma(v[u + 1], xv[u + 1], s2);
+    }
   }
+  s += s2;
   const int rem = mw % U;  // warp-uniform
   if (rem > 0) {
     row_chunk<G, U>(p, p1, col, vals, x, v, xv);

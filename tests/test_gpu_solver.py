@@ -98,6 +98,60 @@ def test_spmv_powerlaw_several_segments_per_cta(cbg, orc):
     assert np.all(np.abs(y - ref) <= 2 * np.maximum(lens, 1) * 2.0 ** -53 * absum + 1e-300)
     assert abs(nrm.item() - orc.dot2(y, y)) <= 1e-12 * orc.dot2(y, y)
 
+
+def exact_norm_rhs(n, seed):
+    """Integer entries in [-1000, 1000] plus one entry c chosen so that ||b||^2 = k^2 exactly: with
+    S the odd sum of the other squares and S = d e (d <= e, both odd), c = (e - d) / 2 and
+    k = (e + d) / 2. Every partial sum of squares is an integer below 2^53, so any summation order
+    gives ||b|| = k bit for bit."""
+    import math
+
+    rng = np.random.default_rng(seed)
+    while True:
+        p = rng.integers(-1000, 1001, n - 1)
+        if int((p.astype(np.int64) ** 2).sum()) % 2 == 0:
+            p[0] = p[0] + 1 if p[0] < 1000 else p[0] - 1
+        S = int((p.astype(np.int64) ** 2).sum())
+        d = math.isqrt(S)
+        d -= 1 - d % 2
+        while d >= 3 and S % d:
+            d -= 2
+        if d < 3:
+            continue
+        e = S // d
+        c, k = (e - d) // 2, (e + d) // 2
+        if k >= 1 << 26:
+            continue
+        b = np.insert(p.astype(np.float64), int(rng.integers(0, n)), float(c))
+        assert int((b.astype(np.int64) ** 2).sum()) == k * k
+        return b, float(k)
+
+
+@pytest.mark.parametrize("cycle", ["auto", "streamed"])
+@pytest.mark.parametrize("fmt,l", [("fp64", 32), ("fp32", 32), ("fp16", 32), ("bf16", 32), ("frsz2", 16),
+                                   ("frsz2", 21), ("frsz2", 32)])
+def test_first_basis_vector_is_the_oracles_inside_a_solve(cbg, orc, fmt, l, cycle):
+    """The stored v_1 = r_0 / beta of a C1 solve (Fig. 1 step 1, x_0 = 0), bit for bit against the
+    oracle's encoding of the correctly rounded quotient. b has integer entries whose norm is an
+    exact integer, so the GPU's beta has the oracle's bits whatever its reduction order, and every
+    stored byte then depends only on the division and the encoder."""
+    A, _ = c1()
+    b, k = exact_norm_rhs(A.n, 3)
+    Ad = A.to("cuda")
+    S = cbg.Solver(Ad.row_ptr, Ad.col, Ad.vals, restart=50, tol=1e-10, fmt=fmt, frsz2_bits=l, cycle=cycle)
+    assert (S.cycle_cluster > 0) == (cycle == "auto")
+    x = torch.zeros(A.n, dtype=torch.float64, device="cuda")
+    S.start(torch.from_numpy(b).cuda(), x)
+    S.stream.synchronize()  # advance launches a cycle once it sees the start's residual finished
+    S.advance(1)
+    got = S.basis_vector(0)
+    S.stream.synchronize()
+    got = got.cpu().numpy()
+    S.close()  # mid-solve: the context is released without finishing
+    f = orc.FORMAT_NAMES[fmt]
+    ref = orc.decode(*orc.encode(b / k, f, l), A.n, f, l)
+    assert np.array_equal(got.view(np.uint64), ref.view(np.uint64)), int((got != ref).sum())
+
 def test_bad_matrix_rejected(cbg):
     A, _ = c1()
     Ad = A.to("cuda")
