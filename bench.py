@@ -741,6 +741,8 @@ def main():
     ap.add_argument("--no-extras", action="store_true", help="skip the format sweep, e2e, solve and CPU legs")
     ap.add_argument("--serving-requests", type=int, default=100, help="requests of the serving leg (0 skips it)")
     ap.add_argument("--serving-nmax", type=float, default=1e6, help="largest request n of the serving leg")
+    ap.add_argument("--serving-only", action="store_true", help="only the serving leg (--serving-requests, "
+                    "--serving-nmax)")
     ap.add_argument("--solve-c1", action="store_true", help="only the 64x64 solves to 1e-10 (on-chip and "
                     "streamed cycles)")
     ap.add_argument("--solve-c3", default="", help="comma-separated basis formats (fp64, fp32, fp16, bf16, "
@@ -817,6 +819,13 @@ def main():
     if args.sweep:
         if rank == 0:
             print(json.dumps({"sweep": sweep(pkg, torch, device, args.sweep, args.rhs, target_iters=args.target_iters)}))
+        if dist:
+            dist.barrier()
+            dist.destroy_process_group()
+        return
+    if args.serving_only:
+        if rank == 0:
+            print(json.dumps({"serving": serving(pkg, torch, device, args.serving_requests, 1e4, args.serving_nmax)}))
         if dist:
             dist.barrier()
             dist.destroy_process_group()
