@@ -64,11 +64,17 @@ namespace cbg {
 #ifndef CBG_DOT_STAGES_32
 #define CBG_DOT_STAGES_32 2
 #endif
+// resident CTAs per SM the binary32 dot's registers are capped for
+#ifndef CBG_DOT_F32_MINB
+#define CBG_DOT_F32_MINB 3
+#endif
 
-// FDot<16, true> is the same pipeline over a basis stored as binary16 (64 bytes per 32-value block,
-// as an l = 16 block, and no exponent words): every value below 2 in magnitude is an exact integer
-// in units of 2^-24 (fp16_fixed), so a block's dot is the same exact integer sum.
-template <int L, bool H = false>
+// FDot<16, K> for K = 1 (binary16) and K = 2 (bfloat16) is the same pipeline over a basis stored as
+// 16-bit values (64 bytes per 32-value block, as an l = 16 block, and no exponent words): every
+// binary16 value below 2 in magnitude is an exact integer in units of 2^-24 (fp16_fixed), and a
+// bfloat16 block goes on a block fixed point on the fly (block_dot_bf16), so a block's dot is the
+// same exact integer sum.
+template <int L, int K = 0>
 struct FDot {
   // 128 threads (blocks) per tile; 256 at l = 16, whose 8 KB per-vector copies then grow to 16 KB
   // (3.7% faster there)
@@ -77,19 +83,20 @@ struct FDot {
   static constexpr int kVps = L == 16 ? CBG_DOT_VPS_16 : (L == 21 ? CBG_DOT_VPS_21 : CBG_DOT_VPS_32);
   static constexpr int kStages = L == 16 ? CBG_DOT_STAGES_16 : (L == 21 ? CBG_DOT_STAGES_21 : CBG_DOT_STAGES_32);
   static constexpr int kCodeBytes = kThreads * L * 4;
-  static constexpr int kVecBytes = kCodeBytes + (H ? 0 : kThreads * 4);  // one vector's codes and exponents
+  static constexpr int kVecBytes = kCodeBytes + (K ? 0 : kThreads * 4);  // one vector's codes and exponents
   static constexpr int kStageBytes = kVps * kVecBytes;
   static size_t smem_bytes(int nvec) {
     return (size_t)kStages * kStageBytes + (size_t)kWarps * nvec * 8 + 2 * kStages * 8 + 16;
   }
 };
 
-template <int L, bool H>
+template <int L, int K>
 __device__ __forceinline__ void dot_body(const BasisView& B, int nvec, const double* __restrict__ w,
                                          double* __restrict__ out, double* __restrict__ partials,
                                          unsigned int* counter, int* err, const Gate& gate) {
-  static_assert(!H || L == 16, "binary16 blocks have the l = 16 layout");
-  using C = FDot<L, H>;
+  static_assert(K == 0 || L == (K == 3 ? 32 : 16), "16-bit values use the l = 16 layout, binary32 the l = 32 one");
+  constexpr bool H = K != 0;  // a cast format: no exponent words
+  using C = FDot<L, K>;
   constexpr int T = C::kThreads, S = C::kStages;
   if (gate_skip(gate)) return;
   extern __shared__ __align__(128) uint8_t smem[];
@@ -220,6 +227,23 @@ __device__ __forceinline__ void dot_body(const BasisView& B, int nvec, const dou
           }
         }
       }
+      // the warp's 32 block sums th * 2^xb of vector vj at a common scale, exactly in integers;
+      // lane vj % 32 keeps vector vj's, and every 32 vectors each lane converts its vector once and
+      // adds it to the warp's per-vector sum (one FP64 instruction per 32 vectors)
+      auto post = [&](int vj, long long th, int xb) {
+        int X;
+        const long long sum = warp_fixed_sum(th, xb, X);
+        if (lane == (vj & 31)) {
+          ks = sum;
+          kx = X;
+        }
+        if ((vj & 31) == 31 || vj == nv - 1) {
+          if (lane <= (vj & 31)) {
+            double* hv = myh + v_lo + (vj & ~31) + lane;
+            *hv = fma_pow2(static_cast<double>(ks), kx, *hv);
+          }
+        }
+      };
 #pragma unroll
       for (int j = 0; j < VPS; ++j) {
         const int vj = vi + j;
@@ -239,6 +263,52 @@ __device__ __forceinline__ void dot_body(const BasisView& B, int nvec, const dou
             // normal.
             th = (a1 << (32 - L)) + ((a0 + (1ll << (L - 6))) >> (L - 5));
             xb = (e > 1 ? static_cast<int>(e) : 1) + ew - 2101;
+          } else if (K == 3) {
+            // binary32: sum = tot 2^(E + ew - 1263) exactly, |tot| < 2^121, rounded once to 61 bits.
+            // The ragged last block and the blocks that are not exact on the block fixed point
+            // take FP64.
+            const int64_t rem = B.n - b * 32;
+            __int128 tot;
+            int E = 0;
+            if (rem >= 32 && block_dot_f32(cw, t, W1, W0, tot, E)) {
+              const unsigned __int128 A = tot < 0 ? -static_cast<unsigned __int128>(tot) : static_cast<unsigned __int128>(tot);
+              const uint64_t hi = static_cast<uint64_t>(A >> 64), lo = static_cast<uint64_t>(A);
+              const int bl = hi ? 128 - __clzll(static_cast<long long>(hi))
+                                : (lo ? 64 - __clzll(static_cast<long long>(lo)) : 0);
+              const int u = bl > 61 ? bl - 61 : 0;
+              th = u ? static_cast<long long>((tot + (static_cast<__int128>(1) << (u - 1))) >> u)
+                     : static_cast<long long>(tot);
+              xb = u + E + ew - 1263;
+            } else {
+              const float* fv = reinterpret_cast<const float*>(cw);
+              const double* wb = w + b * 32;
+              double acc = 0.0;
+#pragma unroll 1
+              for (int k = 0; k < 32; ++k)
+                if (k < rem) acc = fma(static_cast<double>(fv[k]), __ldg(wb + k), acc);
+              split_double(acc, th, xb);
+            }
+          } else if (K == 2) {
+            // bfloat16: sum = (a1 2^27 + a0) 2^(E + ew - 1223) exactly, |a1|, |a0| < 2^55; kept or
+            // rounded to 62 bits as for binary16 below. The ragged last block and the blocks that
+            // are not exact on the block fixed point take FP64.
+            const int64_t rem = B.n - b * 32;
+            int E = 0;
+            if (rem >= 32 && block_dot_bf16(cw, t, W1, W0, a1, a0, E)) {
+              const unsigned long long A = static_cast<unsigned long long>(a1 < 0 ? -a1 : a1);
+              const int bl = 64 - __clzll(static_cast<long long>(A));
+              const int u = bl > 35 ? bl - 35 : 0;
+              th = u == 0 ? (a1 << 27) + a0 : (a1 << (27 - u)) + ((a0 + (1ll << (u - 1))) >> u);
+              xb = u + E + ew - 1223;
+            } else {
+              const uint16_t* hv = reinterpret_cast<const uint16_t*>(cw);
+              const double* wb = w + b * 32;
+              double acc = 0.0;
+#pragma unroll 1
+              for (int k = 0; k < 32; ++k)
+                if (k < rem) acc = fma(widen_f32(static_cast<uint32_t>(hv[k]) << 16), __ldg(wb + k), acc);
+              split_double(acc, th, xb);
+            }
           } else {
             uint32_t emax = 0;
             block_dot_fp16(cw, t, W1, W0, a1, a0, emax);
@@ -265,21 +335,7 @@ __device__ __forceinline__ void dot_body(const BasisView& B, int nvec, const dou
             }
           }
         }
-        // the warp's 32 block sums at a common scale, exactly in integers; lane vj % 32 keeps vector
-        // vj's, and every 32 vectors each lane converts its vector once and adds it to the warp's
-        // per-vector sum (one FP64 instruction per 32 vectors)
-        int X;
-        const long long sum = warp_fixed_sum(th, xb, X);
-        if (lane == (vj & 31)) {
-          ks = sum;
-          kx = X;
-        }
-        if ((vj & 31) == 31 || vj == nv - 1) {
-          if (lane <= (vj & 31)) {
-            double* hv = myh + v_lo + (vj & ~31) + lane;
-            *hv = fma_pow2(static_cast<double>(ks), kx, *hv);
-          }
-        }
+        post(vj, th, xb);
       }
       __syncwarp();
       if (lane == 0 && ok) mbar_arrive(&empty[s]);
@@ -324,16 +380,31 @@ __global__ void __launch_bounds__(FDot<L>::kThreads) k_dot_frsz2(BasisView B, in
                                                                  double* __restrict__ out,
                                                                  double* __restrict__ partials,
                                                                  unsigned int* counter, int* err, Gate gate) {
-  dot_body<L, false>(B, nvec, w, out, partials, counter, err, gate);
+  dot_body<L, 0>(B, nvec, w, out, partials, counter, err, gate);
 }
 
 // The binary16 basis (two resident CTAs of 256 threads: registers capped at 128).
-__global__ void __launch_bounds__(FDot<16, true>::kThreads, 2) k_dot_fp16(BasisView B, int nvec,
+__global__ void __launch_bounds__(FDot<16, 1>::kThreads, 2) k_dot_fp16(BasisView B, int nvec,
                                                                           const double* __restrict__ w,
                                                                           double* __restrict__ out,
                                                                           double* __restrict__ partials,
                                                                           unsigned int* counter, int* err, Gate gate) {
-  dot_body<16, true>(B, nvec, w, out, partials, counter, err, gate);
+  dot_body<16, 1>(B, nvec, w, out, partials, counter, err, gate);
+}
+
+__global__ void __launch_bounds__(FDot<32, 3>::kThreads, CBG_DOT_F32_MINB) k_dot_f32(BasisView B, int nvec, const double* __restrict__ w,
+                                                                  double* __restrict__ out,
+                                                                  double* __restrict__ partials,
+                                                                  unsigned int* counter, int* err, Gate gate) {
+  dot_body<32, 3>(B, nvec, w, out, partials, counter, err, gate);
+}
+
+__global__ void __launch_bounds__(FDot<16, 2>::kThreads, 2) k_dot_bf16(BasisView B, int nvec,
+                                                                          const double* __restrict__ w,
+                                                                          double* __restrict__ out,
+                                                                          double* __restrict__ partials,
+                                                                          unsigned int* counter, int* err, Gate gate) {
+  dot_body<16, 2>(B, nvec, w, out, partials, counter, err, gate);
 }
 
 // ================================================================================================
@@ -430,6 +501,16 @@ __device__ __forceinline__ void load_codes8(const uint32_t* st, int t, uint32_t 
       c[k] = __funnelshift_r(al[a], a + 1 < 6 ? al[a + 1] : 0u, oo) & 0x1FFFFFu;
     }
   }
+}
+
+// w[k0 + k] -= hv * v_k for a thread's 8 binary16 values c (k0 + k < n), in FP64: the rare path of a
+// warp range holding a value of 2 or more, kept out of line so that it does not enlarge the
+// update's loop body (the loop otherwise stalls on instruction fetch).
+__device__ __noinline__ void fp16_axpy8_fp64(double* __restrict__ w, int64_t k0, int64_t n, double hv,
+                                             const uint32_t (&c)[8]) {
+#pragma unroll 1
+  for (int k = 0; k < 8; ++k)
+    if (k0 + k < n) w[k0 + k] = fma(-hv, widen_f16(c[k]), w[k0 + k]);
 }
 
 // H: the basis is stored as binary16 in the l = 16 layout, without exponent words. Its values below 2
@@ -681,10 +762,7 @@ __device__ __forceinline__ void update_body(const BasisView& B, int nvec_arg, co
                   }
                 }
               } else if (active) {  // a value of magnitude >= 2 (not a Krylov vector): FP64
-                const double hv = negate ? -hcoef[g0 + v + j] : hcoef[g0 + v + j];
-#pragma unroll 1
-                for (int k = 0; k < 8; ++k)
-                  if (k0 + k < B.n) w[k0 + k] = fma(-hv, widen_f16(c[k]), w[k0 + k]);
+                fp16_axpy8_fp64(w, k0, B.n, negate ? -hcoef[g0 + v + j] : hcoef[g0 + v + j], c);
               }
             }
           }
@@ -848,18 +926,25 @@ const void* fnp(K k) {
 }  // namespace
 
 // The dot of a binary16 basis on the integer pipeline (FDot<16, true>).
-int fp16_dot_launch(const BasisView& B, int nvec, const double* w, double* out, double* partials,
+int int_dot_launch(const BasisView& B, int nvec, const double* w, double* out, double* partials,
                     unsigned int* counter, int* err, const Gate& gate, int max_grid, cudaStream_t stream) {
-  using C = FDot<16, true>;
-  const void* fn = fnp(k_dot_fp16);
-  const size_t smem = C::smem_bytes(nvec);
+  const bool f32 = B.fmt == CBG_FP32, bf = B.fmt == CBG_BF16;
+  const int T = f32 ? FDot<32, 3>::kThreads : FDot<16, 1>::kThreads;
+  static_assert(FDot<16, 1>::kThreads == FDot<16, 2>::kThreads, "one configuration for the 16-bit formats");
+  const void* fn = f32 ? fnp(k_dot_f32) : (bf ? fnp(k_dot_bf16) : fnp(k_dot_fp16));
+  const size_t smem = f32 ? FDot<32, 3>::smem_bytes(nvec) : FDot<16, 1>::smem_bytes(nvec);
   int gx, full;
-  int st = basis_launch_config(fn, C::kThreads, smem, (B.n + 31) / 32, C::kThreads / 8, max_grid, &gx, &full);
+  int st = basis_launch_config(fn, T, smem, (B.n + 31) / 32, T / 8, max_grid, &gx, &full);
   if (st) return st;
   const dim3 grid(gx, dot_vector_split(gx, full, nvec, max_grid));
-  k_dot_fp16<<<grid, C::kThreads, smem, stream>>>(B, nvec, w, out, partials, counter, err, gate);
+  if (f32)
+    k_dot_f32<<<grid, T, smem, stream>>>(B, nvec, w, out, partials, counter, err, gate);
+  else if (bf)
+    k_dot_bf16<<<grid, T, smem, stream>>>(B, nvec, w, out, partials, counter, err, gate);
+  else
+    k_dot_fp16<<<grid, T, smem, stream>>>(B, nvec, w, out, partials, counter, err, gate);
   cudaError_t e = cudaGetLastError();
-  return e == cudaSuccess ? CBG_OK : cuda_fail(e, "fp16 dot launch");
+  return e == cudaSuccess ? CBG_OK : cuda_fail(e, "integer-pipeline cast dot launch");
 }
 
 int frsz2_dot_launch(const BasisView& B, int nvec, const double* w, double* out, double* partials,

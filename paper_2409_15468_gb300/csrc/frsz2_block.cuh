@@ -121,6 +121,119 @@ __device__ __forceinline__ void block_dot_fp16(const uint32_t* cw, int t, const 
   a0 = a0e + a0o;
 }
 
+// Integer dot of one block of 32 bfloat16 values (64 bytes, the layout of an l = 16 block) with the
+// thread's W registers, in the order and with the bank rotation of block_dot<16>. The block goes on
+// a fixed point on the fly. With E the largest exponent field of the block, every value v becomes
+// the integer c = v 2^(148 - E), |c| < 2^22: an 8-bit significand lands on an integer exactly when
+// its exponent field is at least E - 14.
+// - Pass 1 finds E and the smallest nonzero magnitude. It returns false, leaving the block to the
+//   caller's FP64 path, when a nonzero value lies lower than that, or when E is below 21 or 255
+//   (the scale 2^(148 - E) then leaves the binary32 range, or the block holds an infinity or NaN).
+// - Pass 2 forms each c with one binary32 FMA, v 2^(148 - E) + 1.5 2^23, exact in the binade
+//   [2^23, 2^24), whose bits minus those of 1.5 2^23 are c. The products are block_dot's.
+// On true the block's sum is (a1 2^27 + a0) 2^(E + ew - 1223), with W in units of 2^(ew - 1075).
+__device__ __forceinline__ bool block_dot_bf16(const uint32_t* cw, int t, const int32_t (&W1)[32],
+                                               const int32_t (&W0)[32], long long& a1, long long& a0, int& E) {
+  const uint4* c4 = reinterpret_cast<const uint4*>(cw);
+  uint32_t mx = 0, mn = 0xFFFFFFFFu;  // largest magnitude bits; smallest nonzero one, minus 1
+#pragma unroll
+  for (int c = 0; c < 4; ++c) {
+    const uint4 q = c4[(c + (t >> 1)) & 3];
+    const uint32_t wv[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll
+    for (int h = 0; h < 4; ++h) {
+      const uint32_t lo = wv[h] & 0x7FFFu, hi = (wv[h] >> 16) & 0x7FFFu;
+      mx = max(mx, max(lo, hi));
+      mn = min(mn, min(lo - 1u, hi - 1u));  // a zero wraps to the largest value
+    }
+  }
+  a1 = a0 = 0;
+  E = static_cast<int>(mx >> 7);
+  if (mx == 0) return true;  // every value is zero
+  const int emin = max(static_cast<int>((mn + 1u) >> 7), 1);
+  if (E < 21 || E > 254 || emin + 14 < E) return false;
+  const float S = __uint_as_float(static_cast<uint32_t>(275 - E) << 23);  // 2^(148 - E)
+  constexpr float kMagic = 12582912.0f;                                   // 1.5 2^23
+  constexpr int32_t kMagicBits = 0x4B400000;
+  long long a1e = 0, a0e = 0, a1o = 0, a0o = 0;
+#pragma unroll
+  for (int c = 0; c < 4; ++c) {
+    const uint4 q = c4[(c + (t >> 1)) & 3];
+    const uint32_t wv[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll
+    for (int h = 0; h < 4; ++h) {
+      const int32_t lo = __float_as_int(fmaf(__uint_as_float(wv[h] << 16), S, kMagic)) - kMagicBits;
+      const int32_t hi = __float_as_int(fmaf(__uint_as_float(wv[h] & 0xFFFF0000u), S, kMagic)) - kMagicBits;
+      mac_wide(a1e, lo, W1[8 * c + 2 * h]);
+      mac_wide(a0e, lo, W0[8 * c + 2 * h]);
+      mac_wide(a1o, hi, W1[8 * c + 2 * h + 1]);
+      mac_wide(a0o, hi, W0[8 * c + 2 * h + 1]);
+    }
+  }
+  a1 = a1e + a1o;
+  a0 = a0e + a0o;
+  return true;
+}
+
+// Integer dot of one block of 32 binary32 values (128 bytes, the layout of an l = 32 block) with
+// the thread's W registers, in the order and with the bank rotation of block_dot<32>. The block
+// goes on a fixed point on the fly. With E the largest exponent field of the block, a normal value
+// with significand M (24 bits, leading 1 included) and exponent field e becomes the integer
+// c = M 2^(e - E + 38) < 2^62, so v = c 2^(E - 188).
+// - Pass 1 finds E and the smallest nonzero magnitude. It returns false, leaving the block to the
+//   caller's FP64 path, when a nonzero value lies more than 38 binades below the largest, when
+//   the block holds a subnormal, or when it holds an infinity or NaN.
+// - Pass 2 splits each c into 31-bit pieces, c1 = c >> 31 and c0 = c mod 2^31, signs them, and
+//   forms the four exact products c1 W1, c1 W0, c0 W1 and c0 W0 in 64-bit sums.
+// On true, tot is the block's exact sum in units of 2^(E + ew - 1263) (|tot| < 2^121), with W in
+// units of 2^(ew - 1075).
+__device__ __forceinline__ bool block_dot_f32(const uint32_t* cw, int t, const int32_t (&W1)[32],
+                                              const int32_t (&W0)[32], __int128& tot, int& E) {
+  const uint4* c4 = reinterpret_cast<const uint4*>(cw);
+  uint32_t mx = 0, mn = 0xFFFFFFFFu;  // largest magnitude bits; smallest nonzero one, minus 1
+#pragma unroll
+  for (int c = 0; c < 8; ++c) {
+    const uint4 q = c4[(c + t) & 7];
+    const uint32_t f[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const uint32_t m = f[j] & 0x7FFFFFFFu;
+      mx = max(mx, m);
+      mn = min(mn, m - 1u);  // a zero wraps to the largest value
+    }
+  }
+  tot = 0;
+  E = static_cast<int>(mx >> 23);
+  if (mx == 0) return true;  // every value is zero
+  const int emin = static_cast<int>((mn + 1u) >> 23);
+  if (E > 254 || emin == 0 || emin + 38 < E) return false;
+  long long s11 = 0, s10 = 0, s01 = 0, s00 = 0;
+#pragma unroll
+  for (int c = 0; c < 8; ++c) {
+    const uint4 q = c4[(c + t) & 7];
+    const uint32_t f[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int e = static_cast<int>((f[j] >> 23) & 0xFFu);
+      // a zero has e = 0: no leading 1 and a zero shift, so c = 0
+      const uint64_t M = (f[j] & 0x7FFFFFu) | (e ? 0x800000u : 0u);
+      const uint64_t cc = M << (e ? e - E + 38 : 0);
+      const int32_t sg = static_cast<int32_t>(f[j]) >> 31;  // 0 or -1
+      const int32_t c1 = (static_cast<int32_t>(cc >> 31) ^ sg) - sg;
+      const int32_t c0 = (static_cast<int32_t>(cc & 0x7FFFFFFFu) ^ sg) - sg;
+      const int r = 4 * c + j;
+      mac_wide(s11, c1, W1[r]);
+      mac_wide(s10, c1, W0[r]);
+      mac_wide(s01, c0, W1[r]);
+      mac_wide(s00, c0, W0[r]);
+    }
+  }
+  // c W = (c1 2^31 + c0)(W1 2^27 + W0): each 64-bit sum is below 2^63 (32 terms below 2^58)
+  tot = (static_cast<__int128>(s11) << 58) + (static_cast<__int128>(s10) << 31) +
+        (static_cast<__int128>(s01) << 27) + static_cast<__int128>(s00);
+  return true;
+}
+
 // Register slot r of the thread's W holds block value w_index(L, t, r) (the order block_dot reads).
 template <int L>
 __device__ __forceinline__ int w_index(int t, int r) {

@@ -74,7 +74,8 @@ int basis_launch_config(const void* fn, int threads, size_t smem, int64_t units,
 int dot_vector_split(int gx, int full, int nvec, int max_grid);
 int frsz2_dot_launch(const BasisView& B, int nvec, const double* w, double* out, double* partials,
                      unsigned int* counter, int* err, const Gate& gate, int max_grid, cudaStream_t stream);
-int fp16_dot_launch(const BasisView& B, int nvec, const double* w, double* out, double* partials,
+// The dot of a binary32, binary16 or bfloat16 basis (B.fmt) on the FRSZ2 kernels' integer pipeline.
+int int_dot_launch(const BasisView& B, int nvec, const double* w, double* out, double* partials,
                     unsigned int* counter, int* err, const Gate& gate, int max_grid, cudaStream_t stream);
 int fp16_update_launch(const BasisView& B, int nvec, const int* nvec_dev, const double* h, int negate, double* w,
                        double* partials, unsigned int* counter, int* err, const NormEpilogue& epi, const Gate& gate,

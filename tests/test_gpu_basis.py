@@ -243,3 +243,50 @@ def test_fp16_values_of_two_and_more(cbg, orc, op):
         # the FP64 path's bound (the cast formats') added to the integer path's
         tol = fp16_update_tolerance(Vhat, h, w, idx) + 4 * nvec * 2.0 ** -53 * terms.sum(axis=0)
         assert np.all(np.abs(out - ref) <= tol), (np.abs(out - ref) / tol).max()
+
+
+@pytest.mark.parametrize("fmt", [3, 1])
+def test_cast_dot_block_fixed_point_edges(cbg, orc, fmt):
+    """The bfloat16 (fmt 3) and binary32 (fmt 1) dots put each 32-value block on a fixed point
+    2^(148 - E), resp. 2^(188 - E), on the fly (E the block's largest exponent field) and take FP64
+    for a block they cannot hold exactly: a nonzero value more than 14, resp. 38, binades below the
+    largest, a bfloat16 block of tiny values (E below 21), subnormals, the ragged last block. Blocks
+    built for each branch: one value scaled down by exactly that many binades (exact unless the
+    block's largest lies higher) or by more (FP64), all-zero blocks, tiny values, single nonzero
+    values and subnormals; against the oracle's compensated dot of the decoded values, with the dot
+    tolerance."""
+    span, tiny, sub = {3: (14, 2.0 ** -120, 2.0 ** -130), 1: (38, 2.0 ** -100, 2.0 ** -140)}[fmt]
+    n, nvec = 32 * 700 + 19, 9
+    rng = np.random.default_rng(91 + fmt)
+    V = rng.standard_normal((nvec, n)) * 2.0 ** -8
+    nb = (n + 31) // 32
+    for i in range(nvec):
+        for b in range(nb):
+            blk = V[i, 32 * b: 32 * b + 32]
+            kind = (b + 3 * i) % 8
+            if kind == 1:  # one value `span` binades down
+                blk[rng.integers(0, blk.size)] *= 2.0 ** -span
+            elif kind == 2:  # further down: FP64
+                blk[rng.integers(0, blk.size)] *= 2.0 ** -rng.integers(span + 2, span + 40)
+            elif kind == 3:
+                blk[:] = 0.0
+            elif kind == 4:  # tiny values
+                blk *= tiny
+            elif kind == 5:  # one nonzero value
+                keep = rng.integers(0, blk.size)
+                v = blk[keep]
+                blk[:] = 0.0
+                blk[keep] = v
+            elif kind == 6:  # subnormals next to normal values: FP64
+                blk[::5] = sub
+    B = cbg.BasisStorage(n, nvec, fmt, 32)
+    Vd = torch.from_numpy(V).cuda()
+    for i in range(nvec):
+        B.store(i, Vd[i].contiguous())
+    Vhat = np.stack([orc.decode(*orc.encode(V[i], fmt, 32), n, fmt, 32) for i in range(nvec)])
+    for seed in range(2):
+        w = np.random.default_rng(100 + seed).standard_normal(n) * np.exp2(rng.integers(-30, 30, n))
+        got = B.dot(nvec, torch.from_numpy(w).cuda()).cpu().numpy()
+        ref = orc.basis_dot(Vhat, w)
+        tol = dot_tolerance(Vhat, w)
+        assert np.all(np.abs(got - ref) <= tol), (seed, (np.abs(got - ref) / tol).max())
