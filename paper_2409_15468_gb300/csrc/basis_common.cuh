@@ -45,6 +45,18 @@ __device__ __forceinline__ void mac_wide(long long& acc, int32_t a, int32_t b) {
   acc += p;
 }
 
+// *p += v on a shared-memory counter with acquire-release ordering at CTA scope; returns the old
+// value. The warp whose increment completes a count sees every access the other warps made before
+// theirs.
+__device__ __forceinline__ unsigned atom_add_acq_rel_cta(unsigned* p, unsigned v) {
+  unsigned old;
+  asm volatile("atom.acq_rel.cta.shared::cta.add.u32 %0, [%1], %2;"
+               : "=r"(old)
+               : "r"(static_cast<uint32_t>(__cvta_generic_to_shared(p))), "r"(v)
+               : "memory");
+  return old;
+}
+
 // x / 2^d rounded to nearest (ties up) for |x| < 2^62 and d >= 0.
 __device__ __forceinline__ long long round_shift_right(long long x, int d) {
   if (d <= 0) return x;

@@ -539,6 +539,9 @@ __device__ __forceinline__ void update_body(const BasisView& B, int nvec_arg, co
   uint64_t* full = reinterpret_cast<uint64_t*>(red + C::kWarps);
   uint64_t* empty = full + S;
   uint64_t* ebar = empty + S;  // exponent words of the next group ([1] unused, keeps alignment)
+  // per stage s: rel[2 s] counts the warps that released it, rel[2 s + 1] is the last unit issued
+  // into it (the "empty" slots hold these counters)
+  unsigned* rel = reinterpret_cast<unsigned*>(empty);
   int* flags = reinterpret_cast<int*>(ebar + 2);
 
   const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
@@ -567,7 +570,8 @@ __device__ __forceinline__ void update_body(const BasisView& B, int nvec_arg, co
   if (t == 0) {
     for (int s = 0; s < S; ++s) {
       mbar_init(&full[s], 1);
-      mbar_init(&empty[s], C::kWarps);
+      rel[2 * s] = 0;
+      rel[2 * s + 1] = static_cast<unsigned>(s);
     }
     mbar_init(&ebar[0], 1);
     fence_mbar_init();
@@ -603,7 +607,7 @@ __device__ __forceinline__ void update_body(const BasisView& B, int nvec_arg, co
       bulk_g2s(exq + v * NBT, reinterpret_cast<const uint8_t*>(B.exps) + (int64_t)(g0 + v) * B.estride + tb0 * 4,
                ebytes, &ebar[0]);
   };
-  int issued = 0, eissued = 0;  // warp 0: code copies (thread 0) and exponent-group copies issued
+  int issued = 0, eissued = 0;  // the first S code copies (thread 0); exponent-group copies (warp 0)
   if (!H && warp == 0 && ntiles > 0 && nvec > 0) {
     issue_exps(0, 0);
     ++eissued;
@@ -616,11 +620,8 @@ __device__ __forceinline__ void update_body(const BasisView& B, int nvec_arg, co
   double nrm = 0.0;
   int s = 0;            // stage of the current unit and the phase parity of its barriers
   uint32_t ph = 0;
-  int ps = 0;           // stage and parity of the previous unit (refilled by thread 0)
-  uint32_t pph = 0;
-  bool first = true;
+  int pu = 0;           // the current unit
   bool dead = false;    // this warp gave up waiting (warp-uniform; it then only runs to the next barrier)
-  bool rfail = false;   // thread 0 gave up waiting for a stage to be released (no more refills)
   bool aborted = false;
   for (int tile = 0; tile < ntiles && !aborted; ++tile) {
     const int64_t tb0 = b0 + (int64_t)tile * NBT;
@@ -702,17 +703,6 @@ __device__ __forceinline__ void update_body(const BasisView& B, int nvec_arg, co
 #pragma unroll
       for (int k = 0; k < 8; ++k) acc0[k] = acc1[k] = 0;
       for (int v = 0; v < gn; v += VPS) {
-        // lagged refill (thread 0): the stage every warp released in the previous iteration
-        if (t == 0 && !first && issued < total && !rfail && !dead) {
-          if (mbar_wait_bounded(&empty[ps], pph)) {
-            issue(issued);
-            ++issued;
-          } else {
-            rfail = true;
-            flags[0] = 1;
-            atomicOr(err, kDevErrTimeout);
-          }
-        }
         bool ok = false;
         if (!dead) {
           ok = __all_sync(0xffffffffu, mbar_wait_bounded(&full[s], ph));
@@ -767,11 +757,17 @@ __device__ __forceinline__ void update_body(const BasisView& B, int nvec_arg, co
             }
           }
         }
+        // release the stage; the warp that releases it last refills it at once with unit pu + S (a
+        // warp that gave up waiting never releases, so the others give up in turn)
         __syncwarp();
-        if (lane == 0 && ok) mbar_arrive(&empty[s]);
-        ps = s;
-        pph = ph;
-        first = false;
+        if (lane == 0 && ok && atom_add_acq_rel_cta(&rel[2 * s], 1u) == C::kWarps - 1) {
+          rel[2 * s] = 0;
+          if (pu + S < total) {
+            rel[2 * s + 1] = static_cast<unsigned>(pu + S);
+            issue(pu + S);
+          }
+        }
+        ++pu;
         if (++s == S) {
           s = 0;
           ph ^= 1u;
@@ -873,8 +869,10 @@ __device__ __forceinline__ void update_body(const BasisView& B, int nvec_arg, co
   __syncthreads();
   if (flag_read(&flags[0])) {
     if (t == 0) {
-      for (int p = max(0, issued - S); p < issued; ++p)
-        mbar_wait_bounded(&full[p % S], static_cast<uint32_t>((p / S) & 1));
+      for (int st = 0; st < S; ++st) {  // the last unit issued into each stage (complete if consumed)
+        const int p = static_cast<int>(rel[2 * st + 1]);
+        if (p < total) mbar_wait_bounded(&full[st], static_cast<uint32_t>((p / S) & 1));
+      }
       if (eissued > egroups) mbar_wait_bounded(&ebar[0], static_cast<uint32_t>(egroups & 1));
     }
     return;
