@@ -327,7 +327,9 @@ def solve_c3(pkg, torch, device, formats, N: int = 256, restart: int = 100, tol:
     import workloads
 
     if matrix == "c4":
-        A = workloads.powerlaw(1 << 22, seed=2, device=device)
+        # generated on the host, as the oracle's stored solve is (the device generator draws other
+        # random numbers), then moved to the GPU
+        A = workloads.powerlaw(1 << 22, seed=2).to(device)
         desc = (f"power-law random nonsymmetric n={A.n}, nnz={A.nnz} (row lengths min(2000, floor(10 U^-1/1.5))"
                 f", N(0,1) off-diagonals, diag 1.2 x row abs-sum, seed 2)")
     else:
@@ -715,6 +717,56 @@ def cpu_baseline(n_full: int, nvec: int):
                             "sample": f"3 steps over {nvec} x {n1} values, {dt1:.1f} s"}}
 
 
+def oracle_solve_rate(config: str, fmt: str = "frsz2_32", restart: int = 100) -> dict:
+    """The oracle's CB-GMRES on the host, one core, per Arnoldi step at the full size of c3 (256^3
+    convection-diffusion) or c4 (the 2^22-row power-law matrix): one whole restart cycle (restart
+    steps, second passes included) of the same operator at a reduced size (64^3, resp. 2^18 rows)
+    is timed, and its time per step is scaled by the row count (a step's work is linear in n at a
+    fixed restart length). The oracle's memory traffic grows faster than its cache share at the full
+    size, so the scaled figure is a lower bound on the full-size time per step."""
+    import oracle
+    import workloads
+
+    oracle.build()
+    if config == "c3":
+        A = workloads.convdiff(64, 3, (1.0, 1.0, 1.0), 50.0)
+        scale, small = (256 / 64) ** 3, "64^3"
+    else:
+        A = workloads.powerlaw(1 << 18, seed=2)
+        scale, small = float(1 << 4), "2^18 rows"
+    rp, col, vals = A.numpy()
+    b = oracle.spmv(rp, col, vals, np.ones(A.n))
+    f, l = ("frsz2", int(fmt.split("_")[1])) if fmt.startswith("frsz2") else (fmt, 32)
+    t = time.perf_counter()
+    r = oracle.gmres(rp, col, vals, b, restart=restart, tol=1e-300, max_iters=restart,
+                     fmt=oracle.FORMAT_NAMES[f], l=l)
+    dt = time.perf_counter() - t
+    return {"s_per_step_full_size": dt / max(r.iters, 1) * scale, "unit": "s per Arnoldi step", "cores": 1,
+            "format": fmt, "sample": f"one restart cycle ({r.iters} steps, {r.reorths} second passes) on {small}, "
+                                    f"{dt:.1f} s, scaled by n x{scale:g}"}
+
+
+def add_oracle_solve_rates(line: dict) -> None:
+    """cpu_baseline.solves: the oracle's time per Arnoldi step on c3 and c4 (oracle_solve_rate), and
+    extrapolated to the step count the GPU solve of the same system took to reach 1e-10; with the
+    oracle's full solve time from its stored record when one is committed (one core, on the host
+    that wrote it)."""
+    out = {}
+    for config, key in (("c3", "time_to_tol_c3"), ("c4", "time_to_tol_c4")):
+        rate = oracle_solve_rate(config)
+        gpu = line.get(key, {}).get("frsz2_32")
+        if gpu:
+            rate["gpu_steps_to_tol"] = gpu["iters"]
+            rate["time_to_tol_extrapolated_s"] = rate["s_per_step_full_size"] * gpu["iters"]
+            rate["gpu_seconds"] = gpu["seconds"]
+        ref = stored_oracle_solve(config, "frsz2_32")
+        if ref:
+            rate["stored_full_solve"] = {"seconds": ref["oracle_seconds"], "steps": ref["iters"], "cores": 1,
+                                         "host": ref.get("host")}
+        out[config] = rate
+    line["cpu_baseline"]["solves"] = out
+
+
 # ------------------------------------------------------------------------------------------------
 
 def max_over_ranks(dist, value: float, device) -> float:
@@ -743,6 +795,8 @@ def main():
     ap.add_argument("--serving-nmax", type=float, default=1e6, help="largest request n of the serving leg")
     ap.add_argument("--serving-only", action="store_true", help="only the serving leg (--serving-requests, "
                     "--serving-nmax)")
+    ap.add_argument("--no-solve-baseline", action="store_true",
+                    help="skip the oracle's per-step timing of the c3/c4 solves in cpu_baseline")
     ap.add_argument("--solve-c1", action="store_true", help="only the 64x64 solves to 1e-10 (on-chip and "
                     "streamed cycles)")
     ap.add_argument("--solve-c3", default="", help="comma-separated basis formats (fp64, fp32, fp16, bf16, "
@@ -916,6 +970,8 @@ def main():
         if args.serving_requests > 0:
             line["serving"] = serving(pkg, torch, device, args.serving_requests, 1e4, args.serving_nmax)
         line["cpu_baseline"] = cpu_baseline(args.n, args.nvec)
+        if not args.no_solve_baseline:
+            add_oracle_solve_rates(line)
     if dist:
         dist.barrier()
         dist.destroy_process_group()

@@ -75,3 +75,14 @@ def test_max_over_ranks_single_process():
     import bench
 
     assert bench.max_over_ranks(None, 3.25, None) == 3.25
+
+
+def test_oracle_solve_rate_scales_one_cycle():
+    """cpu_baseline.solves times one whole restart cycle of the oracle at a reduced size and scales
+    its time per Arnoldi step by the row count; with a 5-step cycle on the power-law operator."""
+    sys.path.insert(0, ROOT)
+    import bench
+
+    r = bench.oracle_solve_rate("c4", restart=5)
+    assert r["s_per_step_full_size"] > 0 and r["cores"] == 1 and r["unit"] == "s per Arnoldi step"
+    assert "one restart cycle (5 steps" in r["sample"] and "x16" in r["sample"]

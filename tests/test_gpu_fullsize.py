@@ -8,10 +8,11 @@ compute one by one:
   - the update at sampled elements: against the oracle over all 100 vectors;
   - the fused norm: against the oracle's compensated norm of the whole result.
   Tolerances are those of test_gpu_basis.py.
-* the 256^3 convection-diffusion solve to 1e-10 (b = A 1 from the oracle's SpMV, restart 100) with
+* the 256^3 convection-diffusion solve (and the 4M-row power-law solve) to 1e-10 (b = A 1 from the
+  oracle's SpMV, restart 100) with
   the FRSZ2-32 and the fp64 basis: the final residual recomputed with the oracle's SpMV, and the
   solve compared with the oracle's own solve of the same system, which takes the oracle hours and
-  is therefore stored as tests/golden/solve_c3_<format>.json (written by
+  is therefore stored as tests/golden/solve_{c3,c4}_<format>.json (written by
   tests/golden/make_solve_references.py): iterations within 2%, second-pass counts that differ by no more than the
   step counts do, equal breakdown counts, and the solution within 1e-8 (relative) at the stored sample of indices.
 """
@@ -102,9 +103,29 @@ def c3(orc):
     return Ah.to("cuda"), (rp, col, vals), bh
 
 
+@pytest.fixture(scope="module")
+def c4(orc):
+    Ah = workloads.powerlaw(1 << 22, seed=2)
+    rp, col, vals = Ah.numpy()
+    bh = orc.spmv(rp, col, vals, np.ones(Ah.n))
+    return Ah.to("cuda"), (rp, col, vals), bh
+
+
 @pytest.mark.parametrize("fmt,l,name", [("frsz2", 32, "frsz2_32"), ("fp64", 32, "fp64")])
 def test_c3_solve_full_size(cbg, orc, c3, fmt, l, name):
-    A, (rp, col, vals), bh = c3
+    full_size_solve(cbg, orc, c3, fmt, l, "c3", name)
+
+
+@pytest.mark.parametrize("fmt,l,name", [("frsz2", 32, "frsz2_32"), ("fp64", 32, "fp64")])
+def test_c4_solve_full_size(cbg, orc, c4, fmt, l, name):
+    """The 4M-row power-law system (Pareto row lengths 10-2000, seed 2), b = A 1, restart 100, to
+    1e-10, against the oracle's stored solve tests/golden/solve_c4_<format>.json; its rows take the
+    segment-sorted long-row SpMV."""
+    full_size_solve(cbg, orc, c4, fmt, l, "c4", name)
+
+
+def full_size_solve(cbg, orc, system, fmt, l, config, name):
+    A, (rp, col, vals), bh = system
     S = cbg.Solver(A.row_ptr, A.col, A.vals, restart=100, tol=1e-10, fmt=fmt, frsz2_bits=l)
     x = torch.zeros(A.n, dtype=torch.float64, device="cuda")
     r = S.solve(torch.from_numpy(bh).cuda(), x)
@@ -114,7 +135,7 @@ def test_c3_solve_full_size(cbg, orc, c3, fmt, l, name):
     rrn = orc.nrm2(bh - orc.spmv(rp, col, vals, xh)) / orc.nrm2(bh)
     assert rrn <= 1.0001e-10
     assert abs(rrn - r.true_rrn) <= 1e-3 * rrn
-    path = os.path.join(ROOT, "tests", "golden", f"solve_c3_{name}.json")
+    path = os.path.join(ROOT, "tests", "golden", f"solve_{config}_{name}.json")
     if not os.path.exists(path):
         pytest.skip(f"no stored oracle solve {os.path.basename(path)}")
     with open(path) as f:
