@@ -294,12 +294,23 @@ __device__ __forceinline__ void dot_body(const BasisView& B, int nvec, const dou
             // are not exact on the block fixed point take FP64.
             const int64_t rem = B.n - b * 32;
             int E = 0;
-            if (rem >= 32 && block_dot_bf16(cw, t, W1, W0, a1, a0, E)) {
+            __int128 tot = 0;
+            const int kind = rem >= 32 ? block_dot_bf16(cw, t, W1, W0, a1, a0, tot, E) : 2;
+            if (kind == 0) {
               const unsigned long long A = static_cast<unsigned long long>(a1 < 0 ? -a1 : a1);
               const int bl = 64 - __clzll(static_cast<long long>(A));
               const int u = bl > 35 ? bl - 35 : 0;
               th = u == 0 ? (a1 << 27) + a0 : (a1 << (27 - u)) + ((a0 + (1ll << (u - 1))) >> u);
               xb = u + E + ew - 1223;
+            } else if (kind == 1) {  // the wide path: tot 2^(E + ew - 1263), rounded once to 61 bits
+              const unsigned __int128 A = tot < 0 ? -static_cast<unsigned __int128>(tot) : static_cast<unsigned __int128>(tot);
+              const uint64_t hi = static_cast<uint64_t>(A >> 64), lo = static_cast<uint64_t>(A);
+              const int bl = hi ? 128 - __clzll(static_cast<long long>(hi))
+                                : (lo ? 64 - __clzll(static_cast<long long>(lo)) : 0);
+              const int u = bl > 61 ? bl - 61 : 0;
+              th = u ? static_cast<long long>((tot + (static_cast<__int128>(1) << (u - 1))) >> u)
+                     : static_cast<long long>(tot);
+              xb = u + E + ew - 1263;
             } else {
               const uint16_t* hv = reinterpret_cast<const uint16_t*>(cw);
               const double* wb = w + b * 32;

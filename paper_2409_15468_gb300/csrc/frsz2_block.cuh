@@ -126,14 +126,20 @@ __device__ __forceinline__ void block_dot_fp16(const uint32_t* cw, int t, const 
 // a fixed point on the fly. With E the largest exponent field of the block, every value v becomes
 // the integer c = v 2^(148 - E), |c| < 2^22: an 8-bit significand lands on an integer exactly when
 // its exponent field is at least E - 14.
-// - Pass 1 finds E and the smallest nonzero magnitude. It returns false, leaving the block to the
-//   caller's FP64 path, when a nonzero value lies lower than that, or when E is below 21 or 255
-//   (the scale 2^(148 - E) then leaves the binary32 range, or the block holds an infinity or NaN).
+// - Pass 1 finds E and the smallest nonzero magnitude. When a nonzero value lies lower than
+//   E - 14, or E is below 21 (the scale 2^(148 - E) then leaves the binary32 range), the block
+//   takes the wide path instead, as long as every nonzero value lies within 54 binades of the
+//   largest: c = M 2^(max(e, 1) - E + 54) < 2^62 (M the 8-bit significand, e the exponent field,
+//   E now the effective largest, at least 1), so v = c 2^(E - 188); c in 31-bit pieces, four
+//   exact products; it returns 1 with the exact sum tot in units of 2^(E + ew - 1263). It returns
+//   2, leaving the block to the caller's FP64 path, when a value lies further down or the block
+//   holds an infinity or NaN.
 // - Pass 2 forms each c with one binary32 FMA, v 2^(148 - E) + 1.5 2^23, exact in the binade
 //   [2^23, 2^24), whose bits minus those of 1.5 2^23 are c. The products are block_dot's.
-// On true the block's sum is (a1 2^27 + a0) 2^(E + ew - 1223), with W in units of 2^(ew - 1075).
-__device__ __forceinline__ bool block_dot_bf16(const uint32_t* cw, int t, const int32_t (&W1)[32],
-                                               const int32_t (&W0)[32], long long& a1, long long& a0, int& E) {
+// On 0 the block's sum is (a1 2^27 + a0) 2^(E + ew - 1223), with W in units of 2^(ew - 1075).
+__device__ __forceinline__ int block_dot_bf16(const uint32_t* cw, int t, const int32_t (&W1)[32],
+                                              const int32_t (&W0)[32], long long& a1, long long& a0,
+                                              __int128& tot, int& E) {
   const uint4* c4 = reinterpret_cast<const uint4*>(cw);
   uint32_t mx = 0, mn = 0xFFFFFFFFu;  // largest magnitude bits; smallest nonzero one, minus 1
 #pragma unroll
@@ -149,9 +155,37 @@ __device__ __forceinline__ bool block_dot_bf16(const uint32_t* cw, int t, const 
   }
   a1 = a0 = 0;
   E = static_cast<int>(mx >> 7);
-  if (mx == 0) return true;  // every value is zero
+  if (mx == 0) return 0;  // every value is zero
   const int emin = max(static_cast<int>((mn + 1u) >> 7), 1);
-  if (E < 21 || E > 254 || emin + 14 < E) return false;
+  if (E > 254) return 2;
+  if (E < 21 || emin + 14 < E) {
+    E = max(E, 1);
+    if (emin + 54 < E) return 2;
+    // the wide path: c = M 2^(max(e, 1) - E + 54) < 2^62 in 31-bit pieces, four exact products
+    long long s11 = 0, s10 = 0, s01 = 0, s00 = 0;
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      const uint4 q = c4[(c + (t >> 1)) & 3];
+      const uint32_t wv[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll
+      for (int k = 0; k < 8; ++k) {
+        const uint32_t h = (k & 1) ? wv[k >> 1] >> 16 : wv[k >> 1] & 0xFFFFu;
+        const int e = static_cast<int>((h >> 7) & 0xFFu);
+        const uint64_t M = (h & 0x7Fu) | (e ? 0x80u : 0u);
+        const uint64_t cc = M ? M << (max(e, 1) - E + 54) : 0;
+        const int32_t sg = (h & 0x8000u) ? -1 : 0;
+        const int32_t c1 = (static_cast<int32_t>(cc >> 31) ^ sg) - sg;
+        const int32_t c0 = (static_cast<int32_t>(cc & 0x7FFFFFFFu) ^ sg) - sg;
+        mac_wide(s11, c1, W1[8 * c + k]);
+        mac_wide(s10, c1, W0[8 * c + k]);
+        mac_wide(s01, c0, W1[8 * c + k]);
+        mac_wide(s00, c0, W0[8 * c + k]);
+      }
+    }
+    tot = (static_cast<__int128>(s11) << 58) + (static_cast<__int128>(s10) << 31) +
+          (static_cast<__int128>(s01) << 27) + static_cast<__int128>(s00);
+    return 1;
+  }
   const float S = __uint_as_float(static_cast<uint32_t>(275 - E) << 23);  // 2^(148 - E)
   constexpr float kMagic = 12582912.0f;                                   // 1.5 2^23
   constexpr int32_t kMagicBits = 0x4B400000;
@@ -172,7 +206,7 @@ __device__ __forceinline__ bool block_dot_bf16(const uint32_t* cw, int t, const 
   }
   a1 = a1e + a1o;
   a0 = a0e + a0o;
-  return true;
+  return 0;
 }
 
 // Integer dot of one block of 32 binary32 values (128 bytes, the layout of an l = 32 block) with

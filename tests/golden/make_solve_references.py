@@ -23,6 +23,8 @@ rounding-level changes of the input: the short bases turn such changes into diff
 spaces). The oracle uses IEEE operations only, so these numbers are the same on every host.
 
 Usage: python tests/golden/make_solve_references.py {c3,c4,c3m,c1} {fp64,fp32,fp16,bf16,frsz2_16,frsz2_21,frsz2_32} [--band K]
+       python tests/golden/make_solve_references.py CONFIG FORMAT --fingerprint   (adds the matrix
+       fingerprint to an existing record)
 The fixture is written to tests/golden/solve_<config>_<format>.json.
 """
 from __future__ import annotations
@@ -80,8 +82,35 @@ def sample_indices(n: int) -> np.ndarray:
     return idx
 
 
+def matrix_sha256(rp, col, vals) -> str:
+    """Fingerprint of the CSR arrays (int32 row pointers and columns, float64 values): a record is
+    only comparable with a solve of the same matrix, and the power-law generator draws from the
+    host's random number generator."""
+    h = hashlib.sha256()
+    for a, t in ((rp, np.int32), (col, np.int32), (vals, np.float64)):
+        h.update(np.ascontiguousarray(a, dtype=t).tobytes())
+    return h.hexdigest()
+
+
+def fingerprint(config: str, fname: str) -> None:
+    """Adds the matrix fingerprint and nnz to an existing record (regenerating the matrix)."""
+    path = os.path.join(HERE, f"solve_{config}_{fname}.json")
+    with open(path) as f:
+        rec = json.load(f)
+    rp, col, vals = matrix(config).numpy()
+    rec["nnz"] = int(col.size)
+    rec["matrix_sha256"] = matrix_sha256(rp, col, vals)
+    with open(path, "w") as f:
+        json.dump(rec, f, indent=1)
+        f.write("\n")
+    print(path, rec["nnz"], rec["matrix_sha256"])
+
+
 def main():
     config, fname = sys.argv[1], sys.argv[2]
+    if "--fingerprint" in sys.argv:
+        fingerprint(config, fname)
+        return
     fmt, l = (oracle.FRSZ2, int(fname.split("_")[1])) if fname.startswith("frsz2") else (oracle.FORMAT_NAMES[fname], 32)
     A = matrix(config)
     rp, col, vals = A.numpy()
@@ -99,6 +128,8 @@ def main():
         "cite": "Fig. 1 (restarted CB-GMRES); Methodology (x0 = 0, Eq. 4 relative residual)",
         "config": config,
         "matrix": CONFIGS[config],
+        "nnz": int(col.size),
+        "matrix_sha256": matrix_sha256(rp, col, vals),
         "rhs": b_desc,
         "format": fname,
         "restart": restart,

@@ -248,9 +248,11 @@ def test_fp16_values_of_two_and_more(cbg, orc, op):
 @pytest.mark.parametrize("fmt", [3, 1])
 def test_cast_dot_block_fixed_point_edges(cbg, orc, fmt):
     """The bfloat16 (fmt 3) and binary32 (fmt 1) dots put each 32-value block on a fixed point
-    2^(148 - E), resp. 2^(188 - E), on the fly (E the block's largest exponent field) and take FP64
-    for a block they cannot hold exactly: a nonzero value more than 14, resp. 38, binades below the
-    largest, a bfloat16 block of tiny values (E below 21), subnormals, the ragged last block. Blocks
+    2^(148 - E), resp. 2^(188 - E), on the fly (E the block's largest exponent field). A bfloat16
+    block with a nonzero value more than 14 binades below the largest, or with E below 21, takes a
+    wide integer path (62-bit codes, within 54 binades); FP64 takes what neither holds: bfloat16
+    subnormals beside normal values, a binary32 value more than 38 binades down or subnormal, the
+    ragged last block. Blocks
     built for each branch: one value scaled down by exactly that many binades (exact unless the
     block's largest lies higher) or by more (FP64), all-zero blocks, tiny values, single nonzero
     values and subnormals; against the oracle's compensated dot of the decoded values, with the dot
