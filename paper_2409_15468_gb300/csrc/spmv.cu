@@ -12,10 +12,10 @@
 // Matrices with long rows (mean >= 12 nonzeros, e.g. power-law row lengths): a CTA takes 512
 // consecutive rows and sorts them in shared memory by a length key (the exact length below 64,
 // eighths of an octave above), longest first. Each length class gets its own number G of lanes per
-// row, 8-16 nonzeros per lane, so a warp serves 32/G rows of nearly equal length. GB300 issues an
-// FP64 warp instruction at full cost whatever its active lanes, and the SpMV's FP64 time is close
-// to its HBM time, so the warp issues exactly as many FMAs as its longest lane needs (no chunk
-// padding). The row sum costs log2(G) shuffle-adds; the rows of a segment are read close together
+// row, at most 8 nonzeros per lane up to 255, so a warp serves 32/G rows of nearly equal length,
+// each in one round of loads. GB300 issues an FP64 warp instruction at full cost whatever its
+// active lanes, and the SpMV's FP64 time is close to its HBM time, so the warp issues exactly as
+// many FMAs as its longest lane needs (no chunk padding). The row sum costs log2(G) shuffle-adds; the rows of a segment are read close together
 // in time, so the sectors that neighbouring rows share come from DRAM once (a global sort by
 // length scattered them: 1.47x the algorithmic DRAM bytes).
 #include "common.cuh"
@@ -82,12 +82,16 @@ constexpr int kExactKeys = 64;                // rows shorter than this are keye
 constexpr int kLenKeys = kExactKeys + 5 * 8;  // then 8 keys per octave up to 2047, the last one capped
 constexpr int kLaneClasses = 6;               // G = 32, 16, 8, 4, 2, 1 lanes per row
 // the sort keys of lane class c (G = 32 >> c) are [kClassLo[c], kClassLo[c - 1]), kClassLo[-1] = kLenKeys
-__constant__ int kClassLo[kLaneClasses] = {kExactKeys + 16, kExactKeys + 8, kExactKeys, 32, 16, 0};
+// at most 8 nonzeros per lane below 256, one chunk of loads: G = 1 up to 8, 2 up to 16, 4 up to 32,
+// 8 up to 63, 16 up to 127, else 32
+__constant__ int kClassLo[kLaneClasses] = {kExactKeys + 8, kExactKeys, 33, 17, 9, 0};
 
 // Sort key of a row of `len` nonzeros: the length itself below 64, else its octave and the three
 // bits after the leading one (lengths within 12.5% share a key); 2048 and more share the top key.
-// Keys ascend with the length, and each lane class is a contiguous range of keys: G = 1 below 16
-// nonzeros, 2 below 32, 4 below 64, 8 below 128, 16 below 256, else 32 (8-16 nonzeros per lane).
+// Keys ascend with the length, and each lane class is a contiguous range of keys: G = 1 up to 8
+// nonzeros, 2 up to 16, 4 up to 32, 8 up to 63, 16 up to 127, else 32 (at most 8 nonzeros per lane
+// below 256, so that a row's loads are in flight together: one round trip of column and value
+// loads, then x gathers).
 __device__ __forceinline__ int len_key(int len) {
   if (len < kExactKeys) return len;
   const int b = 31 - __clz(len);

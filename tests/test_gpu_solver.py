@@ -54,7 +54,8 @@ def test_spmv(cbg, orc, matrix):
 def test_spmv_every_length_bucket(cbg, orc, n):
     """Long rows (mean length 12 or more) are sorted within 512-row segments by a length key (the
     exact length below 64, eighths of an octave above, one key for 2048 and more) and get 1 to 32
-    lanes per row by length. Rows of every length from 0 (empty) to 80, and log-uniform lengths up
+    lanes per row by length (at most 8 nonzeros per lane below 256). Rows of every length from 0
+    (empty) to 80, and log-uniform lengths up
     to 3 000, in a random order, against the oracle: every exact key, every per-lane count modulo
     the load chunk, and every lane class; the fused norm too. (The residual form b - A x runs in the
     power-law solves of this file.)"""
