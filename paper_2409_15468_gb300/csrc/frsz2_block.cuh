@@ -268,6 +268,15 @@ __device__ __forceinline__ bool block_dot_f32(const uint32_t* cw, int t, const i
   return true;
 }
 
+// tot rounded once to 61 bits: returns th with tot = th 2^u (nearest, ties up), u >= 0 in *u.
+__device__ __forceinline__ long long round_i128(__int128 tot, int& u) {
+  const unsigned __int128 A = tot < 0 ? -static_cast<unsigned __int128>(tot) : static_cast<unsigned __int128>(tot);
+  const uint64_t hi = static_cast<uint64_t>(A >> 64), lo = static_cast<uint64_t>(A);
+  const int bl = hi ? 128 - __clzll(static_cast<long long>(hi)) : (lo ? 64 - __clzll(static_cast<long long>(lo)) : 0);
+  u = bl > 61 ? bl - 61 : 0;
+  return u ? static_cast<long long>((tot + (static_cast<__int128>(1) << (u - 1))) >> u) : static_cast<long long>(tot);
+}
+
 // Register slot r of the thread's W holds block value w_index(L, t, r) (the order block_dot reads).
 template <int L>
 __device__ __forceinline__ int w_index(int t, int r) {

@@ -347,7 +347,7 @@ __global__ void __launch_bounds__(kOcThreads, 1) k_cycle_onchip(OnchipArgs a, Oc
             acc[q] += scale_pow2(static_cast<double>(th), x + L - 5);
           }
         }
-      } else {
+      } else if (F == CBG_FP64) {
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
           const int i = lane + 32 * q;
@@ -357,6 +357,83 @@ __global__ void __launch_bounds__(kOcThreads, 1) k_cycle_onchip(OnchipArgs a, Oc
 #pragma unroll
             for (int k = 0; k < 32; ++k) d[k & 3] = fma(cast_at<F>(sb, b * 32 + k), wb[k], d[k & 3]);
             acc[q] += (d[0] + d[1]) + (d[2] + d[3]);
+          }
+        }
+      } else {
+        // binary32, binary16, bfloat16: the streamed dot's exact integer block dot (a block fixed
+        // point of the stored values against the 54-bit fixed point of w), one rounding and one
+        // conversion per (vector, block); a block it cannot hold exactly takes FP64 FMAs
+        constexpr int WL = F == CBG_FP32 ? 32 : 16;
+        const int ew = __reduce_max_sync(0xffffffffu, eff_exp(wb[lane]));
+        int2* wt = s.gt + warp * 32;
+        {
+          int32_t w1, w0;
+          to_block_fixed(wb[lane], ew, w1, w0);
+          wt[lane] = make_int2(w1, w0);
+        }
+        __syncwarp();
+        int32_t W1[32], W0[32];
+#pragma unroll
+        for (int r = 0; r < 32; ++r) {
+          const int2 wv = wt[w_index<WL>(lane, r)];
+          W1[r] = wv.x;
+          W0[r] = wv.y;
+        }
+        __syncwarp();  // the table is rewritten for the warp's next block
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const int i = lane + 32 * q;
+          if (i < nv) {
+            const uint8_t* sb = s.codes + (size_t)i * lay.slot_bytes;
+            const uint32_t* cw = reinterpret_cast<const uint32_t*>(sb) + b * WL;  // WL words per block
+            long long th = 0;
+            int xb = 0;
+            bool exact;
+            if (F == CBG_FP16) {
+              uint32_t emax = 0;
+              long long a1, a0;
+              block_dot_fp16(cw, lane, W1, W0, a1, a0, emax);
+              exact = emax <= 15;
+              if (exact) {  // (a1 2^27 + a0) 2^(ew - 1099), kept or rounded to 62 bits
+                const unsigned long long A = static_cast<unsigned long long>(a1 < 0 ? -a1 : a1);
+                const int bl = 64 - __clzll(static_cast<long long>(A));
+                const int u = bl > 35 ? bl - 35 : 0;
+                th = u == 0 ? (a1 << 27) + a0 : (a1 << (27 - u)) + ((a0 + (1ll << (u - 1))) >> u);
+                xb = u + ew - 1099;
+              }
+            } else if (F == CBG_BF16) {
+              long long a1, a0;
+              __int128 tot = 0;
+              int E = 0;
+              const int kind = block_dot_bf16(cw, lane, W1, W0, a1, a0, tot, E);
+              exact = kind < 2;
+              if (kind == 0) {
+                const unsigned long long A = static_cast<unsigned long long>(a1 < 0 ? -a1 : a1);
+                const int bl = 64 - __clzll(static_cast<long long>(A));
+                const int u = bl > 35 ? bl - 35 : 0;
+                th = u == 0 ? (a1 << 27) + a0 : (a1 << (27 - u)) + ((a0 + (1ll << (u - 1))) >> u);
+                xb = u + E + ew - 1223;
+              } else if (kind == 1) {
+                th = round_i128(tot, xb);
+                xb += E + ew - 1263;
+              }
+            } else {
+              __int128 tot = 0;
+              int E = 0;
+              exact = block_dot_f32(cw, lane, W1, W0, tot, E);
+              if (exact) {
+                th = round_i128(tot, xb);
+                xb += E + ew - 1263;
+              }
+            }
+            if (exact) {
+              acc[q] += scale_pow2(static_cast<double>(th), xb);
+            } else {
+              double d[4] = {0.0, 0.0, 0.0, 0.0};
+#pragma unroll 1
+              for (int k = 0; k < 32; ++k) d[k & 3] = fma(cast_at<F>(sb, b * 32 + k), wb[k], d[k & 3]);
+              acc[q] += (d[0] + d[1]) + (d[2] + d[3]);
+            }
           }
         }
       }
@@ -721,9 +798,15 @@ OcLayout oc_layout(int32_t n, int m, int fmt, int l, int cl) {
     int64_t words = nb * l;
     words += ((l - words) % 32 + 32) % 32;
     slot = words * 4;
+  } else if (fmt == CBG_FP64) {
+    slot = rup(rows * 8, 128) + 8;  // lane i of a warp reading slot i: distinct banks
   } else {
-    const int es = fmt == CBG_FP64 ? 8 : (fmt == CBG_FP32 ? 4 : 2);
-    slot = rup(rows * es, 128) + es;  // lane i of a warp reading slot i: distinct banks
+    // binary32 and the 16-bit formats: the integer block dot reads 16-byte chunks of slot i in lane
+    // i in the rotation of block_dot<32>, resp. <16>: the FRSZ2 strides for l = 32, resp. 16
+    const int64_t lw = fmt == CBG_FP32 ? 32 : 16;
+    int64_t words = rows * (fmt == CBG_FP32 ? 4 : 2) / 4;
+    words += ((lw - words) % 32 + 32) % 32;
+    slot = words * 4;
   }
   const int64_t expw = fmt == CBG_FRSZ2 ? (nb | 1) : 0;
   const int64_t off_exps = rup(M1 * slot, 16);
