@@ -445,7 +445,7 @@ __global__ void __launch_bounds__(FDot<16, 2>::kThreads, 2) k_dot_bf16(BasisView
 #define CBG_UPD_MINB_21 4
 #endif
 #ifndef CBG_UPD_MINB_32
-#define CBG_UPD_MINB_32 4
+#define CBG_UPD_MINB_32 5
 #endif
 #ifndef CBG_UPD_STAGES
 #define CBG_UPD_STAGES 2
@@ -462,12 +462,17 @@ struct FUpd {
   static constexpr int kBlocks = kThreads / 4;
   static constexpr int kVps = 4;  // basis vectors per stage
   static constexpr int kStages = S;
-  static constexpr int kGroup = 32;
   // resident CTAs per SM the register allocation is capped for (measured per code width: l = 16,
-  // at 256 threads, with a few spills at 3; l = 21 with 4; l = 32 runs 4 by shared memory and uses
-  // the registers for an early load of w); the deep pipeline runs one CTA per SM
+  // at 256 threads, with a few spills at 3; l = 21 with 4; l = 32 with 5 at 96 registers, 2.4%
+  // faster than 4 at 128 with an early load of w); the deep pipeline runs one CTA per SM
   static constexpr int kMinBlocks =
       S == 12 ? 1 : (L == 32 ? CBG_UPD_MINB_32 : (L == 21 ? CBG_UPD_MINB_21 : CBG_UPD_MINB_16));
+  // vectors per group; five l = 32 CTAs per SM take groups of 28, whose smaller coefficient and
+  // exponent tables (1.5 KB less) let five CTAs' shared memory fit in an SM up to restart 128, and
+  // leave out the early load of w, whose 16 registers do not fit under the cap of 96
+  static constexpr int kGroup = (L == 32 && kMinBlocks >= 5) ? 28 : 32;
+  static constexpr bool kEarlyW = L == 32 && kMinBlocks <= 4;
+  static_assert(kGroup % 4 == 0 && kGroup % kVps == 0, "a group is whole stages, split over 4 threads");
   static constexpr int kVecBytes = kBlocks * L * 4;
   static constexpr int kStageBytes = kVps * kVecBytes;
   // dynamic smem: stages | coefficient table [kGroup][kBlocks] (int2) | exponent words of one group
@@ -642,7 +647,7 @@ __device__ __forceinline__ void update_body(const BasisView& B, int nvec_arg, co
     // l = 32: this thread's 8 values of w are loaded now and arrive while the tile streams (1% at
     // l = 32; at l = 16 and 21 the registers are better spent on the pipeline)
     double wpre[8];
-    if (L == 32 && active && k0 + 8 <= B.n) {
+    if (C::kEarlyW && active && k0 + 8 <= B.n) {
       const double2* pw = reinterpret_cast<const double2*>(w + k0);
 #pragma unroll
       for (int i = 0; i < 4; ++i) {
@@ -845,7 +850,7 @@ __device__ __forceinline__ void update_body(const BasisView& B, int nvec_arg, co
       if (k0 + 8 <= B.n) {
         double2* p = reinterpret_cast<double2*>(w + k0);
         double cur[8];
-        if (L == 32) {
+        if (C::kEarlyW) {
 #pragma unroll
           for (int i = 0; i < 8; ++i) cur[i] = wpre[i];
         } else {

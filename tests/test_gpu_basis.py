@@ -84,7 +84,7 @@ def test_dot(cbg, orc, fmt, l, n, nvec):
 
 @pytest.mark.parametrize("fmt,l", FORMATS)
 @pytest.mark.parametrize("n,nvec", [(1, 1), (77, 3), (4096 + 45, 7), (70000, 20), (30000 + 13, 66),
-                                    (20000, 100)])
+                                    (20000, 100), (300000 + 13, 66), (160000 + 7, 101)])
 def test_update(cbg, orc, fmt, l, n, nvec):
     B, Vhat, exps = make_basis(cbg, orc, n, nvec, fmt, l, seed=3 * n + nvec)
     rng = np.random.default_rng(n + 5)
