@@ -144,11 +144,7 @@ __global__ void __launch_bounds__(CastCfg::kThreads) k_dot_cast(BasisView B, int
   __syncthreads();
   for (int v = v_lo + t; v < v_hi; v += T) partials[(size_t)cid * nvec + v] = hpart[v];
   if (arrive_last(counter, nctas, &flags[0])) {
-    for (int v = warp; v < nvec; v += T / 32) {
-      const int y = vector_slice(v, nvec, gridDim.y);
-      const double sum = warp_sum_strided(partials + (size_t)y * gridDim.x * nvec + v, gridDim.x, nvec);
-      if (lane == 0) out[v] = sum;
-    }
+    slice_sums<2, 8>(partials, nvec, gridDim.x, gridDim.y, out, warp, T / 32);  // measured best here
     if (t == 0) *counter = 0;
   }
 }

@@ -24,6 +24,59 @@ __device__ __forceinline__ int vector_slice(int v, int nvec, int slices) {
   return y;
 }
 
+// The dots' final sums, in the CTA that arrives last: out[v] for every v < nvec is the sum of
+// vector v's partials (partials[(y gx + x) nvec + v] over the gx CTAs x of its slice y). Warp w of
+// `warps` takes vectors w, w + warps, w + 2 warps, ..., K at a time. Each sum is formed in
+// warp_sum_strided's order (lane-strided sums, then the xor tree), so it is bit-identical to that;
+// the K sums of a warp are independent, and the lane loop is unrolled U times (0: the compiler's
+// choice), so that their loads and adds overlap.
+// the FRSZ2 and integer-pipeline dots' shape (4 and 4 measured best against 1 and the compiler's
+// unroll, 8 and 2, 2 and 8; the binary64 dot takes 2 and 8)
+#ifndef CBG_DOT_SUM_K
+#define CBG_DOT_SUM_K 4
+#endif
+#ifndef CBG_DOT_SUM_U
+#define CBG_DOT_SUM_U 4
+#endif
+template <int K, int U>
+__device__ __forceinline__ void slice_sums(const double* partials, int nvec, int gx, int slices, double* out,
+                                           int warp, int warps) {
+  const int lane = threadIdx.x & 31;
+  const int mine = warp < nvec ? (nvec - warp + warps - 1) / warps : 0;  // vectors of this warp
+  for (int c0 = 0; c0 < mine; c0 += K) {
+    const double* p[K];
+    double s[K];
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      const int v = warp + warps * (c0 + k < mine ? c0 + k : c0);  // past the end: a repeat, not stored
+      p[k] = partials + (size_t)vector_slice(v, nvec, slices) * gx * nvec + v;
+      s[k] = 0.0;
+    }
+    if constexpr (U == 0) {
+      for (int i = lane; i < gx; i += 32) {
+#pragma unroll
+        for (int k = 0; k < K; ++k) s[k] += __ldcg(p[k] + (size_t)i * nvec);
+      }
+    } else {
+#pragma unroll U
+      for (int i = lane; i < gx; i += 32) {
+#pragma unroll
+        for (int k = 0; k < K; ++k) s[k] += __ldcg(p[k] + (size_t)i * nvec);
+      }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+#pragma unroll
+      for (int k = 0; k < K; ++k) s[k] += __shfl_xor_sync(0xffffffffu, s[k], o);
+    }
+    if (lane == 0) {
+#pragma unroll
+      for (int k = 0; k < K; ++k)
+        if (c0 + k < mine) out[warp + warps * (c0 + k)] = s[k];
+    }
+  }
+}
+
 __device__ __forceinline__ bool gate_skip(const Gate& g) {
   if (g.stop && *(volatile const int*)g.stop) return true;
   if (g.need && !*(volatile const int*)g.need) return true;

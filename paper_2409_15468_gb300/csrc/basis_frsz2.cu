@@ -64,6 +64,19 @@ namespace cbg {
 #ifndef CBG_DOT_STAGES_32
 #define CBG_DOT_STAGES_32 2
 #endif
+// a dot CTA takes at least 1/CBG_DOT_MIN_DIV of a tile's blocks; vectors are split over CTAs when
+// that leaves the GPU underfilled. Whole tiles (1) keep every thread busy at 10^4-10^6 rows, where
+// an eighth of a tile per CTA left most threads idle: at 110 592 rows the dot took 28.7 us instead
+// of 56 us per launch; unchanged at 2^24 rows
+#ifndef CBG_DOT_MIN_DIV
+#define CBG_DOT_MIN_DIV 1
+#endif
+// the update takes the deep pipeline (one CTA per SM) while fewer than one CTA per SM would get
+// CBG_UPD_DEEP_BLOCKS blocks (32: up to about 155 000 rows; 23.5 instead of 26.1 us per launch at
+// 110 592 rows)
+#ifndef CBG_UPD_DEEP_BLOCKS
+#define CBG_UPD_DEEP_BLOCKS 32
+#endif
 // resident CTAs per SM the binary32 dot's registers are capped for
 #ifndef CBG_DOT_F32_MINB
 #define CBG_DOT_F32_MINB 3
@@ -377,11 +390,7 @@ __device__ __forceinline__ void dot_body(const BasisView& B, int nvec, const dou
     partials[(size_t)cid * nvec + v] = sacc;
   }
   if (arrive_last(counter, nctas, &flags[1])) {
-    for (int v = warp; v < nvec; v += C::kWarps) {
-      const int y = vector_slice(v, nvec, gridDim.y);
-      const double sum = warp_sum_strided(partials + (size_t)y * gridDim.x * nvec + v, gridDim.x, nvec);
-      if (lane == 0) out[v] = sum;
-    }
+    slice_sums<CBG_DOT_SUM_K, CBG_DOT_SUM_U>(partials, nvec, gridDim.x, gridDim.y, out, warp, C::kWarps);
     if (t == 0) *counter = 0;
   }
 }
@@ -948,7 +957,7 @@ int int_dot_launch(const BasisView& B, int nvec, const double* w, double* out, d
   const void* fn = f32 ? fnp(k_dot_f32) : (bf ? fnp(k_dot_bf16) : fnp(k_dot_fp16));
   const size_t smem = f32 ? FDot<32, 3>::smem_bytes(nvec) : FDot<16, 1>::smem_bytes(nvec);
   int gx, full;
-  int st = basis_launch_config(fn, T, smem, (B.n + 31) / 32, T / 8, max_grid, &gx, &full);
+  int st = basis_launch_config(fn, T, smem, (B.n + 31) / 32, T / CBG_DOT_MIN_DIV, max_grid, &gx, &full);
   if (st) return st;
   const dim3 grid(gx, dot_vector_split(gx, full, nvec, max_grid));
   if (f32)
@@ -973,7 +982,7 @@ int frsz2_dot_launch(const BasisView& B, int nvec, const double* w, double* out,
   }
   int gx, full;
   const int thr = B.l == 16 ? FDot<16>::kThreads : (B.l == 21 ? FDot<21>::kThreads : FDot<32>::kThreads);
-  int st = basis_launch_config(fn, thr, smem, (B.n + 31) / 32, thr / 8, max_grid, &gx, &full);
+  int st = basis_launch_config(fn, thr, smem, (B.n + 31) / 32, thr / CBG_DOT_MIN_DIV, max_grid, &gx, &full);
   if (st) return st;
   const dim3 grid(gx, dot_vector_split(gx, full, nvec, max_grid));
   switch (B.l) {
@@ -1013,8 +1022,9 @@ int frsz2_update_launch_l(const BasisView& B, int nvec, const int* nvec_dev, con
   DeviceInfo di;
   int st = device_info(&di);
   if (st) return st;
-  // CTAs the blocks need (8 blocks at least per CTA): fewer than SMs means an underfilled GPU
-  const int64_t need = ((B.n + 31) / 32 + 7) / 8;
+  // CTAs the blocks need (CBG_UPD_DEEP_BLOCKS at least per CTA): fewer than SMs means an
+  // underfilled GPU
+  const int64_t need = ((B.n + 31) / 32 + CBG_UPD_DEEP_BLOCKS - 1) / CBG_UPD_DEEP_BLOCKS;
   if (need < di.sms)
     return frsz2_update_launch_t<L, 12, H>(B, nvec, nvec_dev, h, negate, w, partials, counter, err, epi, gate, 0,
                                            stream);
