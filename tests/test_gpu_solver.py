@@ -2,7 +2,7 @@
 oracle on the 64x64 convection-diffusion system (wind (1, 0.5), Peclet 10, b = A x_true with
 x_true uniform in [-1, 1], seed 0, restart 50, tol 1e-10, x0 = 0) and on a scaled-down 3D
 stencil: the GPU must reach the tolerance, its solution must agree with the oracle's to 1e-8,
-and the Arnoldi step counts must agree within 2% (spec parity bar). Systems this small run
+and the Arnoldi step counts must agree within 2% (the solve parity bar). Systems this small run
 each restart cycle as one thread-block cluster launch (cycle="auto"); the C1 cases also run with
 the streamed kernels (cycle="streamed") to the same bar."""
 import numpy as np
@@ -529,7 +529,7 @@ def _shifted_32x32():
 @pytest.mark.parametrize("cycle", ["auto", "streamed"])
 @pytest.mark.parametrize("fmt", ["fp16", "bf16"])
 def test_gmres_fp16_bf16_strict_bar(cbg, orc, fmt, cycle):
-    """fp16 and bf16 bases at the benchmark spec's own bar, on systems where their step counts are not
+    """fp16 and bf16 bases at the full solve parity bar, on systems where their step counts are not
     chaotic: the shifted 32x32 operator (restart 50) and the power-law matrix with the Jacobi
     preconditioner (restart 30): tolerance reached, steps within 2% of the oracle's,
     ||x - x_oracle|| / ||x_oracle|| <= 1e-8, the same second-pass and breakdown decisions."""

@@ -7,7 +7,7 @@ the basis update runs its two-stage full-grid instance (the grid needs more CTAs
 SMs) and the dot spans the GPU, as at the benchmark's sizes; the smaller solve tests run the on-chip
 cycle or the deep-pipeline instance instead.
 
-Bar (the benchmark spec's): the explicit relative residual reaches the tolerance, the Arnoldi step count
+Bar (the solve parity bar): the explicit relative residual reaches the tolerance, the Arnoldi step count
 is within 2% of the oracle's (for FRSZ2-16 and FRSZ2-21, whose counts move by 2-3% on the oracle
 itself when b moves by one ulp, within 2% of that band), ||x - x_oracle|| / ||x_oracle|| <= 1e-8,
 and the second Gram-Schmidt
